@@ -1,0 +1,626 @@
+/*
+ * hydro_oracle.c -- plain, slow FP64 CPU oracle for the relaxing-TVD
+ * patch-group hydro path of GAMER (Schive, Tsai & Chiueh, arXiv 0907.3390).
+ *
+ * THIS IS TEST INFRASTRUCTURE.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load it.  It shares no code, header,
+ * table or helper with the CUDA library; it is compiled with
+ * -ffp-contract=off so that every operation below rounds once, in the order
+ * written.
+ *
+ * What it computes (paper sections):
+ *   - ideal-gas Euler equations in conservative form, u = (rho, rho v, e)
+ *     (Sec. 2.2, Eqs. MassConserve..EnergyConserve, ThermalEnergy, EOS);
+ *   - the 1-D relaxing TVD scheme: freezing speed c = |v| + c_s, right/left
+ *     moving fluxes F^R, F^L (Eq. LRFlux), first-order upwind half step
+ *     (Eq. MidpointValue), second-order TVD full step with the van Leer
+ *     limiter (Eqs. 2ndTVDFluxCorr, 2ndFluxCorr, vanLeer, 2ndRFlux,
+ *     FullstepValue); minmod is offered as an alternative limiter;
+ *   - Strang dimensional splitting, forward sweep xyz / backward sweep zyx
+ *     with the same dt (Sec. 2.2, last paragraphs);
+ *   - patch groups of 2x2x2 patches of 8^3 cells padded by 3 ghost cells,
+ *     ghost cells copied from same-level neighbours or interpolated with the
+ *     Min-Mod limiter from the level one coarser (Sec. 2.2, Sec. 3.1);
+ *   - restriction (coarse = mean of 8 children) and coarse-fine flux
+ *     correction (Sec. 2.1, step 3 of the level evolution);
+ *   - the CFL time step (Sec. 3.4, Eq. CFL);
+ *   - conservation sums and a positivity count over leaf cells.
+ *
+ * Readings where the paper is silent or loose (each one listed in the design
+ * notes of the repository):
+ *   R1 one call = one sweep set (xyz when order = 0, zyx when order = 1);
+ *   R2 the freezing speed is per cell, |v_normal| + c_s;
+ *   R3 F^R = (c u + F)/2 and F^L = (c u - F)/2, i.e. c (u +- w)/2 with
+ *      w = F/c substituted; w itself is never formed;
+ *   R4 the left-moving TVD flux mirrors Eq. 2ndRFlux with upwind cell n+1;
+ *   R5 van Leer is applied only when the product of the two corrections is
+ *      strictly positive; minmod likewise;
+ *   R6 c_s uses max(P, 0); conserved variables are never floored;
+ *   R7 coarse data used for fine ghost cells is the pre-step coarse state;
+ *   R8 Min-Mod interpolation acts on conserved variables, one slope per axis
+ *      from the two face neighbours of the coarse cell, child value
+ *      U_C + ((sx*Sx + sy*Sy) + sz*Sz)/4 with s* = -1 for the lower child;
+ *   R9 a uniform dt for all levels.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NV 5      /* conserved variables rho, mx, my, mz, e          */
+#define PS 8      /* patch size (cells per axis)                      */
+#define GS 16     /* patch-group size (2 patches per axis)            */
+#define NG 3      /* ghost cells per side (seven-point stencil)       */
+#define PD 22     /* padded patch-group size GS + 2*NG                */
+
+enum { ORC_VANLEER = 0, ORC_MINMOD = 1 };
+enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_MAP = -3 };
+
+/* One refinement level as the oracle sees it.  All arrays are host memory.
+ * u / u_out: [NV][8*n_groups][8][8][8] (x fastest); nbr: [n_groups][26];
+ * parent: [n_groups] (patch index on the level below, NULL on level 0);
+ * child: [8*n_groups] (patch-group index on the level above or -1, NULL if
+ * there is no finer level); face_flux: [n_groups][3][3][NV][16][16] or NULL. */
+typedef struct {
+    int32_t n_groups;
+    int32_t pad_;
+    double dh;
+    const double *u;
+    double *u_out;
+    const int32_t *nbr;
+    const int32_t *parent;
+    const int32_t *child;
+    double *face_flux;
+} orc_level;
+
+/* ---------------------------------------------------------------- limiters */
+
+/* Eq. vanLeer: harmonic combination of the two second-order corrections. */
+double orc_phi_vanleer(double a, double b)
+{
+    if (a * b > 0.0)
+        return 2.0 * a * b / (a + b);
+    return 0.0;
+}
+
+/* minmod: the smaller correction in magnitude when both have one sign. */
+double orc_phi_minmod(double a, double b)
+{
+    if (a * b > 0.0) {
+        double m = fmin(fabs(a), fabs(b));
+        return a > 0.0 ? m : -m;
+    }
+    return 0.0;
+}
+
+static double phi(int limiter, double a, double b)
+{
+    return limiter == ORC_MINMOD ? orc_phi_minmod(a, b) : orc_phi_vanleer(a, b);
+}
+
+/* ------------------------------------------------- cell state and fluxes */
+
+/* Pressure from Eqs. ThermalEnergy and EOS: P = (gamma-1)(e - rho v^2 / 2). */
+double orc_pressure(const double u[NV], double gamma)
+{
+    double rho = u[0];
+    double vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho;
+    double eps = u[4] - 0.5 * rho * (vx * vx + vy * vy + vz * vz);
+    return (gamma - 1.0) * eps;
+}
+
+/* Right- and left-moving fluxes of one cell for a sweep along axis d
+ * (Eq. LRFlux with the freezing speed c = |v_d| + c_s of Sec. 2.2). */
+static void cell_lr_flux(const double u[NV], int d, double gamma,
+                         double FR[NV], double FL[NV])
+{
+    double rho = u[0];
+    double vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho;
+    double eps = u[4] - 0.5 * rho * (vx * vx + vy * vy + vz * vz);
+    double P = (gamma - 1.0) * eps;
+    double cs = sqrt(gamma * fmax(P, 0.0) / rho);
+    double vn = d == 0 ? vx : (d == 1 ? vy : vz);
+    double c = fabs(vn) + cs;
+    double F[NV];
+    /* F = (rho v_d, rho v v_d + P delta, (e + P) v_d) */
+    F[0] = u[1 + d];
+    F[1] = u[1] * vn;
+    F[2] = u[2] * vn;
+    F[3] = u[3] * vn;
+    F[1 + d] = u[1 + d] * vn + P;
+    F[4] = (u[4] + P) * vn;
+    for (int v = 0; v < NV; v++) {
+        FR[v] = 0.5 * (c * u[v] + F[v]);
+        FL[v] = 0.5 * (c * u[v] - F[v]);
+    }
+}
+
+/* One relaxing-TVD step of a 1-D column q[0..L-1] along axis d
+ * (Eqs. MidpointValue, 2ndTVDFluxCorr, 2ndFluxCorr, 2ndRFlux,
+ * FullstepValue).  Cells 3..L-4 of out[] receive the full-step values; the
+ * net interface fluxes G[n] of interface n+1/2 (n = 2..L-4) are returned in
+ * G when it is not NULL. */
+static void tvd_column(const double (*q)[NV], int L, int d, double lam,
+                       double gamma, int limiter, double (*out)[NV],
+                       double (*G)[NV])
+{
+    double (*FR)[NV] = malloc(sizeof(double) * NV * L);
+    double (*FL)[NV] = malloc(sizeof(double) * NV * L);
+    double (*Fh)[NV] = malloc(sizeof(double) * NV * L);
+    double (*uh)[NV] = malloc(sizeof(double) * NV * L);
+    double (*Gl)[NV] = malloc(sizeof(double) * NV * L);
+
+    /* half step: first-order upwind interface flux F_{n+1/2} = F^R_n - F^L_{n+1} */
+    for (int n = 0; n < L; n++)
+        cell_lr_flux(q[n], d, gamma, FR[n], FL[n]);
+    for (int n = 0; n + 1 < L; n++)
+        for (int v = 0; v < NV; v++)
+            Fh[n][v] = FR[n][v] - FL[n + 1][v];
+    for (int n = 1; n + 1 < L; n++)
+        for (int v = 0; v < NV; v++)
+            uh[n][v] = q[n][v] - 0.5 * lam * (Fh[n][v] - Fh[n - 1][v]);
+
+    /* full step: TVD fluxes of the midpoint state */
+    for (int n = 1; n + 1 < L; n++)
+        cell_lr_flux(uh[n], d, gamma, FR[n], FL[n]);
+    for (int n = 2; n + 3 < L; n++) {
+        for (int v = 0; v < NV; v++) {
+            double a = (FR[n][v] - FR[n - 1][v]) / 2.0;
+            double b = (FR[n + 1][v] - FR[n][v]) / 2.0;
+            double FRh = FR[n][v] + phi(limiter, a, b);
+            a = (FL[n + 1][v] - FL[n + 2][v]) / 2.0;
+            b = (FL[n][v] - FL[n + 1][v]) / 2.0;
+            double FLh = FL[n + 1][v] + phi(limiter, a, b);
+            Gl[n][v] = FRh - FLh;
+        }
+    }
+    for (int n = 3; n + 3 < L; n++)
+        for (int v = 0; v < NV; v++)
+            out[n][v] = q[n][v] - lam * (Gl[n][v] - Gl[n - 1][v]);
+    if (G)
+        for (int n = 2; n + 3 < L; n++)
+            for (int v = 0; v < NV; v++)
+                G[n][v] = Gl[n][v];
+    free(FR); free(FL); free(Fh); free(uh); free(Gl);
+}
+
+/* Exported for the column-level tests: q is [L][NV], out receives [L][NV]
+ * with cells 3..L-4 updated (others copied). */
+int orc_tvd_column(const double *q, int L, int d, double lam, double gamma,
+                   int limiter, double *out)
+{
+    if (L < 7 || d < 0 || d > 2)
+        return ORC_ERR_ARG;
+    memcpy(out, q, sizeof(double) * NV * L);
+    tvd_column((const double (*)[NV])q, L, d, lam, gamma, limiter,
+               (double (*)[NV])out, NULL);
+    return ORC_OK;
+}
+
+/* ---------------------------------------------- whole-domain split solver */
+
+/* One sweep set (xyz if order == 0, zyx otherwise) on a whole single-level
+ * domain u[NV][nz][ny][nx] (x fastest).  bc[a] = 0: periodic along axis a,
+ * 1: outflow (zero-gradient).  Every column is padded with 3 ghost cells
+ * from its own boundary rule, updated by the 1-D scheme, and written back. */
+int orc_domain_sweepset(double *u, int nx, int ny, int nz, const int *bc,
+                        double gamma, int limiter, double dt, double dh,
+                        int order)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || dh <= 0.0)
+        return ORC_ERR_ARG;
+    const int n[3] = {nx, ny, nz};
+    const long st[3] = {1, nx, (long)nx * ny};
+    const long ncell = (long)nx * ny * nz;
+    const double lam = dt / dh;
+    for (int s = 0; s < 3; s++) {
+        int a = order == 0 ? s : 2 - s;
+        int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
+        int L = n[a] + 2 * NG;
+        long ncol = (long)n[t1] * n[t2];
+#pragma omp parallel for schedule(static)
+        for (long col = 0; col < ncol; col++) {
+            double (*q)[NV] = malloc(sizeof(double) * NV * L);
+            double (*o)[NV] = malloc(sizeof(double) * NV * L);
+            int i1 = (int)(col % n[t1]), i2 = (int)(col / n[t1]);
+            long base = i1 * st[t1] + i2 * st[t2];
+            for (int k = 0; k < L; k++) {
+                int x = k - NG;
+                if (bc[a] == 0)
+                    x = ((x % n[a]) + n[a]) % n[a];
+                else
+                    x = x < 0 ? 0 : (x >= n[a] ? n[a] - 1 : x);
+                for (int v = 0; v < NV; v++)
+                    q[k][v] = u[v * ncell + base + x * st[a]];
+            }
+            tvd_column((const double (*)[NV])q, L, a, lam, gamma, limiter, o, NULL);
+            for (int k = NG; k < L - NG; k++)
+                for (int v = 0; v < NV; v++)
+                    u[v * ncell + base + (k - NG) * st[a]] = o[k][v];
+            free(q);
+            free(o);
+        }
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------ patch-group form */
+
+static int dir_index(int dx, int dy, int dz)
+{
+    int d = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+    return d < 13 ? d : d - 1;
+}
+
+static int floordiv(int a, int b)
+{
+    int q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0)))
+        q--;
+    return q;
+}
+
+/* Index of cell (x,y,z), 0 <= x,y,z < 16, of patch group g, variable v. */
+static size_t cell_index(const orc_level *L, int g, int v, int x, int y, int z)
+{
+    size_t patch = (size_t)8 * g + (size_t)(((z / PS) * 2 + (y / PS)) * 2 + (x / PS));
+    return ((size_t)v * 8 * L->n_groups + patch) * (PS * PS * PS) +
+           (size_t)(((z % PS) * PS + (y % PS)) * PS + (x % PS));
+}
+
+/* Value of the cell at patch-group-local position (x,y,z) of group g on one
+ * level, -16 <= x,y,z < 32.  Axes whose face neighbour is an outflow
+ * boundary (-2) are clamped into the group first (zero gradient); the rest
+ * are resolved through the neighbour map.  Returns 0 on success, 1 if the
+ * position lies in a region that only exists on the coarser level (-1),
+ * ORC_ERR_MAP on an inconsistent map. */
+static int level_fetch(const orc_level *L, const double *u, int g, int x,
+                       int y, int z, double val[NV])
+{
+    int c[3] = {x, y, z};
+    int o[3];
+    for (int a = 0; a < 3; a++) {
+        o[a] = floordiv(c[a], GS);
+        if (o[a] != 0) {
+            int e[3] = {0, 0, 0};
+            e[a] = o[a];
+            if (L->nbr[(size_t)g * 26 + dir_index(e[0], e[1], e[2])] == -2) {
+                c[a] = c[a] < 0 ? 0 : GS - 1;
+                o[a] = 0;
+            }
+        }
+    }
+    int n = g;
+    if (o[0] || o[1] || o[2])
+        n = L->nbr[(size_t)g * 26 + dir_index(o[0], o[1], o[2])];
+    if (n == -1)
+        return 1;
+    if (n < 0 || n >= L->n_groups)
+        return ORC_ERR_MAP;
+    for (int v = 0; v < NV; v++)
+        val[v] = u[cell_index(L, n, v, c[0] - GS * o[0], c[1] - GS * o[1],
+                              c[2] - GS * o[2])];
+    return 0;
+}
+
+static double minmod2(double a, double b)
+{
+    if (a * b > 0.0) {
+        double m = fmin(fabs(a), fabs(b));
+        return a > 0.0 ? m : -m;
+    }
+    return 0.0;
+}
+
+/* Conservative linear interpolation with the Min-Mod limiter from the level
+ * one coarser (Sec. 2.1 refinement step, Sec. 2.2 ghost zones; reading R8).
+ * (x,y,z) is a fine position relative to fine group g, the coarse data is
+ * the pre-step state of level lv-1 (reading R7). */
+static int prolong_fetch(const orc_level *lv, int l, int g, int x, int y, int z,
+                         double val[NV])
+{
+    if (l == 0 || lv[l].parent == NULL)
+        return ORC_ERR_MAP;
+    const orc_level *C = &lv[l - 1];
+    int P = lv[l].parent[g];
+    if (P < 0 || P >= 8 * C->n_groups)
+        return ORC_ERR_MAP;
+    int gc = P / 8, lp = P % 8;
+    int pc[3] = {lp & 1, (lp >> 1) & 1, (lp >> 2) & 1};
+    int f[3] = {x, y, z};
+    int cc[3], sg[3];
+    for (int a = 0; a < 3; a++) {
+        cc[a] = PS * pc[a] + floordiv(f[a], 2);
+        sg[a] = (f[a] - 2 * floordiv(f[a], 2)) == 0 ? -1 : 1;
+    }
+    double U[NV], Um[NV], Up[NV], S[3][NV];
+    if (level_fetch(C, C->u, gc, cc[0], cc[1], cc[2], U) != 0)
+        return ORC_ERR_MAP;
+    for (int a = 0; a < 3; a++) {
+        int m[3] = {cc[0], cc[1], cc[2]}, p[3] = {cc[0], cc[1], cc[2]};
+        m[a] -= 1;
+        p[a] += 1;
+        if (level_fetch(C, C->u, gc, m[0], m[1], m[2], Um) != 0 ||
+            level_fetch(C, C->u, gc, p[0], p[1], p[2], Up) != 0)
+            return ORC_ERR_MAP;
+        for (int v = 0; v < NV; v++)
+            S[a][v] = minmod2(U[v] - Um[v], Up[v] - U[v]);
+    }
+    for (int v = 0; v < NV; v++) {
+        double t = (sg[0] * S[0][v] + sg[1] * S[1][v]) + sg[2] * S[2][v];
+        val[v] = U[v] + 0.25 * t;
+    }
+    return 0;
+}
+
+/* Exported for the interpolation tests: the 8 children of the coarse cell at
+ * the centre of a 3x3x3 block c[NV][3][3][3] (x fastest), written to
+ * out[NV][2][2][2] (x fastest). */
+int orc_minmod_children(const double *c, double *out)
+{
+    for (int v = 0; v < NV; v++) {
+        const double *b = c + v * 27;
+        double U = b[13];
+        double S[3];
+        S[0] = minmod2(U - b[12], b[14] - U);
+        S[1] = minmod2(U - b[10], b[16] - U);
+        S[2] = minmod2(U - b[4], b[22] - U);
+        for (int k = 0; k < 2; k++)
+            for (int j = 0; j < 2; j++)
+                for (int i = 0; i < 2; i++) {
+                    double sx = i ? 1.0 : -1.0, sy = j ? 1.0 : -1.0, sz = k ? 1.0 : -1.0;
+                    double t = (sx * S[0] + sy * S[1]) + sz * S[2];
+                    out[v * 8 + (k * 2 + j) * 2 + i] = U + 0.25 * t;
+                }
+    }
+    return ORC_OK;
+}
+
+/* Build the padded 22^3 block of group g on level l: interior and
+ * same-level ghosts copied, coarse ghosts interpolated. blk[NV][22][22][22]. */
+static int gather_block(const orc_level *lv, int l, int g, double *blk)
+{
+    const orc_level *L = &lv[l];
+    double val[NV];
+    for (int k = 0; k < PD; k++)
+        for (int j = 0; j < PD; j++)
+            for (int i = 0; i < PD; i++) {
+                int r = level_fetch(L, L->u, g, i - NG, j - NG, k - NG, val);
+                if (r == 1)
+                    r = prolong_fetch(lv, l, g, i - NG, j - NG, k - NG, val);
+                if (r != 0)
+                    return ORC_ERR_MAP;
+                for (int v = 0; v < NV; v++)
+                    blk[((size_t)(v * PD + k) * PD + j) * PD + i] = val[v];
+            }
+    return ORC_OK;
+}
+
+/* Advance the listed patch groups of level l by one sweep set (all groups
+ * if list == NULL): gather, three sweeps on the shrinking regions of
+ * Sec. 3.1 (x on 16x22x22 outputs, y on 16x16x22, z on 16^3 for xyz;
+ * mirrored for zyx), write the 16^3 interior to u_out and, when face_flux
+ * is given, the net fluxes on the interior-relative planes 0, 8, 16 of each
+ * axis for the 16x16 interior rows. */
+int orc_level_advance(const orc_level *lv, int n_levels, int l, double gamma,
+                      int limiter, double dt, int order, const int32_t *list,
+                      int n_list)
+{
+    if (l < 0 || l >= n_levels)
+        return ORC_ERR_ARG;
+    const orc_level *L = &lv[l];
+    int count = list ? n_list : L->n_groups;
+    const double lam = dt / L->dh;
+    int err = ORC_OK;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int it = 0; it < count; it++) {
+        int g = list ? list[it] : it;
+        double *blk = malloc(sizeof(double) * NV * PD * PD * PD);
+        double (*q)[NV] = malloc(sizeof(double) * NV * PD);
+        double (*o)[NV] = malloc(sizeof(double) * NV * PD);
+        double (*G)[NV] = malloc(sizeof(double) * NV * PD);
+        if (gather_block(lv, l, g, blk) != ORC_OK) {
+#pragma omp critical
+            err = ORC_ERR_MAP;
+            free(blk); free(q); free(o); free(G);
+            continue;
+        }
+        const long st[3] = {1, PD, PD * PD};
+        int swept[3] = {0, 0, 0};
+        for (int s = 0; s < 3; s++) {
+            int a = order == 0 ? s : 2 - s;
+            int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
+            int lo1 = swept[t1] ? NG : 0, hi1 = swept[t1] ? NG + GS : PD;
+            int lo2 = swept[t2] ? NG : 0, hi2 = swept[t2] ? NG + GS : PD;
+            for (int i2 = lo2; i2 < hi2; i2++)
+                for (int i1 = lo1; i1 < hi1; i1++) {
+                    long base = i1 * st[t1] + i2 * st[t2];
+                    for (int k = 0; k < PD; k++)
+                        for (int v = 0; v < NV; v++)
+                            q[k][v] = blk[(long)v * PD * PD * PD + base + k * st[a]];
+                    tvd_column((const double (*)[NV])q, PD, a, lam, gamma, limiter, o, G);
+                    for (int k = NG; k < NG + GS; k++)
+                        for (int v = 0; v < NV; v++)
+                            blk[(long)v * PD * PD * PD + base + k * st[a]] = o[k][v];
+                    int interior = i1 >= NG && i1 < NG + GS && i2 >= NG && i2 < NG + GS;
+                    if (L->face_flux && interior) {
+                        for (int p = 0; p < 3; p++)
+                            for (int v = 0; v < NV; v++) {
+                                size_t idx = ((((size_t)g * 3 + a) * 3 + p) * NV + v) * GS * GS +
+                                             (size_t)(i2 - NG) * GS + (i1 - NG);
+                                L->face_flux[idx] = G[NG - 1 + 8 * p][v];
+                            }
+                    }
+                }
+            swept[a] = 1;
+        }
+        for (int v = 0; v < NV; v++)
+            for (int z = 0; z < GS; z++)
+                for (int y = 0; y < GS; y++)
+                    for (int x = 0; x < GS; x++)
+                        L->u_out[cell_index(L, g, v, x, y, z)] =
+                            blk[((size_t)(v * PD + z + NG) * PD + y + NG) * PD + x + NG];
+        free(blk); free(q); free(o); free(G);
+    }
+    return err;
+}
+
+/* Coarse-fine fix-up of level l (Sec. 2.1, step 3): covered coarse cells
+ * become the mean of their 8 children (level l+1 u_out), and leaf coarse
+ * cells next to a refined neighbour patch have the coarse face flux replaced
+ * by the mean of the 4 fine face fluxes (Berger & Colella).  Corrections of
+ * one cell are applied in the order x-, x+, y-, y+, z-, z+. */
+int orc_level_fixup(const orc_level *lv, int n_levels, int l, double dt)
+{
+    if (l < 0 || l + 1 >= n_levels)
+        return ORC_ERR_ARG;
+    const orc_level *C = &lv[l], *F = &lv[l + 1];
+    if (C->child == NULL)
+        return ORC_ERR_ARG;
+    const double lam = dt / C->dh;
+    for (int P = 0; P < 8 * C->n_groups; P++) {
+        int g = P / 8, lp = P % 8;
+        int pc[3] = {lp & 1, (lp >> 1) & 1, (lp >> 2) & 1};
+        int gf = C->child[P];
+        if (gf >= 0) {
+            /* restriction */
+            for (int v = 0; v < NV; v++)
+                for (int k = 0; k < PS; k++)
+                    for (int j = 0; j < PS; j++)
+                        for (int i = 0; i < PS; i++) {
+                            double s = 0.0;
+                            for (int dz = 0; dz < 2; dz++)
+                                for (int dy = 0; dy < 2; dy++)
+                                    for (int dx = 0; dx < 2; dx++)
+                                        s += F->u_out[cell_index(F, gf, v, 2 * i + dx, 2 * j + dy, 2 * k + dz)];
+                            C->u_out[cell_index(C, g, v, PS * pc[0] + i, PS * pc[1] + j, PS * pc[2] + k)] = 0.125 * s;
+                        }
+            continue;
+        }
+        if (C->face_flux == NULL || F->face_flux == NULL)
+            return ORC_ERR_ARG;
+        for (int a = 0; a < 3; a++) {
+            int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
+            for (int s = -1; s <= 1; s += 2) {
+                int q[3] = {pc[0], pc[1], pc[2]};
+                q[a] += s;
+                int gq = g;
+                if (q[a] < 0 || q[a] > 1) {
+                    int e[3] = {0, 0, 0};
+                    e[a] = s;
+                    gq = C->nbr[(size_t)g * 26 + dir_index(e[0], e[1], e[2])];
+                    q[a] = q[a] < 0 ? 1 : 0;
+                }
+                if (gq < 0)
+                    continue;
+                int Q = 8 * gq + (q[2] * 2 + q[1]) * 2 + q[0];
+                int gfq = C->child[Q];
+                if (gfq < 0)
+                    continue;
+                int plane_c = s > 0 ? pc[a] + 1 : pc[a];
+                int plane_f = s > 0 ? 0 : 2;
+                int ca = s > 0 ? PS - 1 : 0;
+                for (int v = 0; v < NV; v++)
+                    for (int b2 = 0; b2 < PS; b2++)
+                        for (int b1 = 0; b1 < PS; b1++) {
+                            int T1 = PS * pc[t1] + b1, T2 = PS * pc[t2] + b2;
+                            double Gc = C->face_flux[((((size_t)g * 3 + a) * 3 + plane_c) * NV + v) * GS * GS +
+                                                     (size_t)T2 * GS + T1];
+                            const double *ff = F->face_flux + ((((size_t)gfq * 3 + a) * 3 + plane_f) * NV + v) * GS * GS;
+                            double Gf = 0.25 * (((ff[(2 * b2) * GS + 2 * b1] + ff[(2 * b2) * GS + 2 * b1 + 1]) +
+                                                 ff[(2 * b2 + 1) * GS + 2 * b1]) + ff[(2 * b2 + 1) * GS + 2 * b1 + 1]);
+                            int xyz[3];
+                            xyz[a] = PS * pc[a] + ca;
+                            xyz[t1] = T1;
+                            xyz[t2] = T2;
+                            size_t ci = cell_index(C, g, v, xyz[0], xyz[1], xyz[2]);
+                            if (s > 0)
+                                C->u_out[ci] = C->u_out[ci] + lam * (Gc - Gf);
+                            else
+                                C->u_out[ci] = C->u_out[ci] - lam * (Gc - Gf);
+                        }
+            }
+        }
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------ CFL and checks */
+
+/* Largest signal speed c_s + max(|vx|,|vy|,|vz|) over all cells of level l
+ * (denominator of Eq. CFL). */
+double orc_level_max_speed(const orc_level *L, double gamma)
+{
+    double smax = 0.0;
+    size_t ncell = (size_t)L->n_groups * 8 * PS * PS * PS;
+    for (size_t i = 0; i < ncell; i++) {
+        double u[NV];
+        for (int v = 0; v < NV; v++)
+            u[v] = L->u[v * ncell + i];
+        double rho = u[0];
+        double vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho;
+        double eps = u[4] - 0.5 * rho * (vx * vx + vy * vy + vz * vz);
+        double P = (gamma - 1.0) * eps;
+        double cs = sqrt(gamma * fmax(P, 0.0) / rho);
+        double s = cs + fmax(fmax(fabs(vx), fabs(vy)), fabs(vz));
+        if (s > smax || s != s)
+            smax = s;
+        if (smax != smax)
+            break;
+    }
+    return smax;
+}
+
+/* Eq. CFL with a safety factor: dt = cfl * min over levels of dh_l / s_l. */
+double orc_cfl_dt(const orc_level *lv, int n_levels, double gamma, double cfl)
+{
+    double dt = INFINITY;
+    for (int l = 0; l < n_levels; l++) {
+        if (lv[l].n_groups == 0)
+            continue;
+        double s = orc_level_max_speed(&lv[l], gamma);
+        double d = lv[l].dh / s;
+        if (d < dt || d != d)
+            dt = d;
+    }
+    return cfl * dt;
+}
+
+/* Sums of u * dV over leaf cells of all levels and the number of leaf cells
+ * with rho <= 0, P <= 0 or a non-finite conserved variable. */
+int orc_check(const orc_level *lv, int n_levels, double gamma, double *sums,
+              int64_t *n_bad)
+{
+    for (int v = 0; v < NV; v++)
+        sums[v] = 0.0;
+    *n_bad = 0;
+    for (int l = 0; l < n_levels; l++) {
+        const orc_level *L = &lv[l];
+        size_t ncell = (size_t)L->n_groups * 8 * PS * PS * PS;
+        double dV = L->dh * L->dh * L->dh;
+        for (size_t i = 0; i < ncell; i++) {
+            size_t patch = i / (PS * PS * PS);
+            if (L->child && L->child[patch] >= 0)
+                continue;
+            double u[NV];
+            int finite = 1;
+            for (int v = 0; v < NV; v++) {
+                u[v] = L->u[v * ncell + i];
+                sums[v] += u[v] * dV;
+                finite &= isfinite(u[v]) ? 1 : 0;
+            }
+            if (!finite || !(u[0] > 0.0) || !(orc_pressure(u, gamma) > 0.0))
+                (*n_bad)++;
+        }
+    }
+    return ORC_OK;
+}
+
+/* Exported for the ghost-zone tests: the padded 22^3 block of group g of
+ * level l, blk[NV][22][22][22] (x fastest). */
+int orc_gather_block(const orc_level *lv, int n_levels, int l, int g, double *blk)
+{
+    if (l < 0 || l >= n_levels || g < 0 || g >= lv[l].n_groups)
+        return ORC_ERR_ARG;
+    return gather_block(lv, l, g, blk);
+}
