@@ -1,0 +1,171 @@
+/*
+ * gamer_hydro.h -- C ABI of the GB300-native relaxing-TVD patch-group hydro
+ * path of GAMER (Schive, Tsai & Chiueh, arXiv 0907.3390).
+ *
+ * The library advances the ideal-gas Euler equations (Sec. 2.2, Eqs.
+ * MassConserve..EOS) on a hierarchy of 8^3-cell patches grouped into 16^3
+ * patch groups (Sec. 3.1) with the second-order relaxing TVD scheme
+ * (Eqs. 1DEuler..FullstepValue), dimensional splitting xyz / zyx (Sec. 2.2),
+ * ghost zones of 3 cells from same-level neighbours or Min-Mod
+ * interpolation from the level one coarser (Sec. 2.2, Sec. 3.1),
+ * restriction and coarse-fine flux correction (Sec. 2.1, step 3), the CFL
+ * time step (Sec. 3.4, Eq. CFL) and conservation / positivity checks.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - All field, map and flux pointers inside gamer_level_t are DEVICE
+ *   pointers owned by the caller; the structs themselves are host memory.
+ * - Conserved state of a level: u[5][8*n_groups][8][8][8], variables
+ *   (rho, rho vx, rho vy, rho vz, e), x fastest; patch group g owns patches
+ *   8g..8g+7, local patch index (pz*2 + py)*2 + px.  Element type float for
+ *   GAMER_FP32 handles, double for GAMER_FP64 handles.
+ * - nbr[n_groups][26]: neighbour d = (dz+1)*9 + (dy+1)*3 + (dx+1) with 13
+ *   (the group itself) skipped: a same-level group index >= 0, -1 when that
+ *   region exists only on the coarser level (ghosts interpolated), -2 for
+ *   an outflow (zero-gradient) domain face.  Periodic wrap is encoded by the
+ *   map.  Ghost cells never come from two levels down (proper nesting,
+ *   Sec. 2.1); maps violating it are rejected with GAMER_ERR_MAP.
+ * - parent[n_groups]: patch index on the level below (NULL on level 0).
+ * - child[8*n_groups]: patch-group index on the level above, or -1 (NULL on
+ *   the finest level).
+ * - Every call returns GAMER_OK (0) or a negative status; the message of the
+ *   last failure is available from gamer_hydro_last_error().  No call
+ *   throws.  Asynchronous calls are ordered on the handle's stream.
+ */
+#ifndef GAMER_HYDRO_H
+#define GAMER_HYDRO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    GAMER_OK = 0,
+    GAMER_ERR_ARG = -1,          /* bad argument                              */
+    GAMER_ERR_CUDA = -2,         /* a CUDA call failed                        */
+    GAMER_ERR_MAP = -3,          /* inconsistent neighbour / parent / child map */
+    GAMER_ERR_TIMEOUT = -4,      /* a bounded device-side wait gave up        */
+    GAMER_ERR_UNSUPPORTED = -5,  /* valid request this build does not offer   */
+    GAMER_ERR_STATE = -6         /* call out of order for the handle          */
+};
+
+enum { GAMER_LIMITER_VANLEER = 0, GAMER_LIMITER_MINMOD = 1 };
+enum { GAMER_FP32 = 0, GAMER_FP64 = 1 };
+
+typedef struct gamer_hydro_s *gamer_hydro_t;
+
+/* One refinement level.  face_flux is optional: [n_groups][3][3][5][16][16]
+ * of the element type (net interface fluxes on the interior-relative planes
+ * 0, 8, 16 of each axis, for the 16x16 interior rows); when NULL and the
+ * hierarchy has more than one level the handle allocates its own. */
+typedef struct {
+    int32_t n_groups;
+    int32_t reserved;
+    double dh;                 /* cell width of this level                   */
+    const void *u;             /* in:  pre-step state                        */
+    void *u_out;               /* out: post-step state, must not alias u     */
+    const int32_t *nbr;
+    const int32_t *parent;
+    const int32_t *child;
+    void *face_flux;
+} gamer_level_t;
+
+/* A hierarchy snapshot.  `version` identifies the maps (nbr, parent,
+ * child, n_groups, dh): the library validates them and builds its work
+ * lists once per version, so a caller that changes a map must change the
+ * version.  The u / u_out pointers may change on every call. */
+typedef struct {
+    int32_t n_levels;
+    int32_t reserved;
+    const gamer_level_t *levels;   /* host array of n_levels entries */
+    uint64_t version;
+} gamer_hierarchy_t;
+
+/* Create a solver handle.
+ * gamma: ratio of specific heats, > 1 (Eq. EOS).
+ * limiter: GAMER_LIMITER_VANLEER (Eq. vanLeer) or GAMER_LIMITER_MINMOD.
+ * ghost_width: must be 3, the ghost depth the seven-point stencil needs
+ *   (Sec. 2.2); other values give GAMER_ERR_UNSUPPORTED.
+ * precision: GAMER_FP32 (batched persistent kernel, FP64 reductions) or
+ *   GAMER_FP64 (plain path, one thread block per patch group).
+ * The handle uses the current CUDA device and the legacy default stream
+ * until gamer_hydro_set_stream().  Every level's sweep parity starts at 0
+ * (xyz).  Errors: GAMER_ERR_ARG (gamma <= 1, unknown limiter/precision,
+ * out == NULL), GAMER_ERR_CUDA. */
+int gamer_hydro_create(double gamma, int limiter, int ghost_width, int precision,
+                       gamer_hydro_t *out);
+
+/* Release the handle and everything it allocated.  NULL is accepted. */
+int gamer_hydro_destroy(gamer_hydro_t h);
+
+/* Stream (a cudaStream_t, or NULL for the legacy stream) on which every
+ * later call of this handle is ordered. */
+int gamer_hydro_set_stream(gamer_hydro_t h, void *cuda_stream);
+
+/* Sweep order of the next advance of `level`: parity 0 = forward xyz,
+ * 1 = backward zyx (Sec. 2.2: forward then backward sweep with one dt).
+ * Every advance of a level flips its parity; these two calls let a caller
+ * read it for a checkpoint and set it on resume.  level in [0, 32). */
+int gamer_hydro_set_parity(gamer_hydro_t h, int level, int parity);
+int gamer_hydro_get_parity(gamer_hydro_t h, int level, int *parity);
+
+/* Time step from Eq. CFL: dt = cfl * min over levels of
+ * dh_l / max over cells of (c_s + max(|vx|,|vy|,|vz|)), read from every
+ * level's u.  The per-group maxima and the reduction are exact (max is
+ * order-independent); the division is FP64.  Synchronous: waits for the
+ * handle's stream and writes *dt_out on the host.  A level whose signal
+ * speed is not finite makes *dt_out NaN. */
+int gamer_hydro_cfl_dt(gamer_hydro_t h, const gamer_hierarchy_t *H, double cfl,
+                       double *dt_out);
+
+/* One sweep set (xyz or zyx by the level's parity) of every patch group of
+ * `level` with time step dt (Sec. 3.1): ghost zones gathered on the device
+ * (same-level copy, Min-Mod interpolation from levels[level-1].u, outflow
+ * clamp), the three sweeps of the relaxing TVD scheme, the 16^3 interior
+ * written to levels[level].u_out and, on multi-level hierarchies, the face
+ * fluxes.  Asynchronous on the handle's stream.  The coarse data read is
+ * levels[level-1].u, so every level of a step must be advanced before any
+ * level is corrected (gamer_hydro_fixup) or swapped by the caller. */
+int gamer_hydro_advance(gamer_hydro_t h, const gamer_hierarchy_t *H, int level,
+                        double dt);
+
+/* Coarse-fine correction of `level` from level+1 (Sec. 2.1, step 3): in
+ * levels[level].u_out, covered cells become the mean of their 8 children
+ * from levels[level+1].u_out, and leaf cells next to a refined neighbour
+ * patch get the coarse face flux replaced by the mean of the 4 fine face
+ * fluxes (Berger-Colella).  dt must be the dt of the advance.  Call for
+ * level = n_levels-2 down to 0 after all advances.  Asynchronous. */
+int gamer_hydro_fixup(gamer_hydro_t h, const gamer_hierarchy_t *H, int level,
+                      double dt);
+
+/* Whole step of the level evolution with a uniform dt: every level
+ * advanced (the FP32 handle uses ONE persistent launch whose device work
+ * queue spans the patch groups of all levels), then the fix-ups from the
+ * finest level down, all captured once per (hierarchy version, pointers,
+ * parity) in a CUDA graph and replayed.  Flips every level's parity.
+ * Asynchronous.  The caller swaps u and u_out of every level afterwards. */
+int gamer_hydro_advance_all(gamer_hydro_t h, const gamer_hierarchy_t *H, double dt);
+
+/* Conservation and positivity check over leaf cells (patches whose child
+ * is -1) of every level's u: sums[v] = sum of u_v * dh^3 (FP64,
+ * deterministic fixed-order reduction), *n_bad = number of cells with
+ * rho <= 0, P <= 0 or a non-finite variable.  Synchronous. */
+int gamer_hydro_check(gamer_hydro_t h, const gamer_hierarchy_t *H, double sums[5],
+                      int64_t *n_bad);
+
+/* gamer_hydro_cfl_dt and gamer_hydro_check in one pass over the data
+ * (either output pointer may be NULL).  Synchronous. */
+int gamer_hydro_diagnose(gamer_hydro_t h, const gamer_hierarchy_t *H, double cfl,
+                         double *dt_out, double sums[5], int64_t *n_bad);
+
+/* Message of the last failed call on this handle ("" if none).  With a NULL
+ * handle, the message of the last failed gamer_hydro_create on this thread.
+ * The string stays valid until the next call on the handle. */
+const char *gamer_hydro_last_error(gamer_hydro_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GAMER_HYDRO_H */

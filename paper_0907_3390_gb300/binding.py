@@ -1,0 +1,259 @@
+"""Thin Python binding of ``libgamer_hydro.so`` (declared in
+``include/gamer_hydro.h``).
+
+The functions below carry the C names and only marshal arguments; every
+step of the computation runs in the library's CUDA kernels.  PyTorch is
+used for device memory and streams only.  Loading fails loudly (raises)
+when the library is missing or cannot be built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+GAMER_OK, GAMER_ERR_ARG, GAMER_ERR_CUDA, GAMER_ERR_MAP = 0, -1, -2, -3
+GAMER_ERR_TIMEOUT, GAMER_ERR_UNSUPPORTED, GAMER_ERR_STATE = -4, -5, -6
+GAMER_LIMITER_VANLEER, GAMER_LIMITER_MINMOD = 0, 1
+GAMER_FP32, GAMER_FP64 = 0, 1
+
+EXPORTS = [
+    "gamer_hydro_create", "gamer_hydro_destroy", "gamer_hydro_set_stream",
+    "gamer_hydro_set_parity", "gamer_hydro_get_parity", "gamer_hydro_cfl_dt",
+    "gamer_hydro_advance", "gamer_hydro_fixup", "gamer_hydro_advance_all",
+    "gamer_hydro_check", "gamer_hydro_diagnose", "gamer_hydro_last_error",
+]
+
+
+class gamer_level_t(C.Structure):
+    _fields_ = [("n_groups", C.c_int32), ("reserved", C.c_int32), ("dh", C.c_double),
+                ("u", C.c_void_p), ("u_out", C.c_void_p), ("nbr", C.c_void_p),
+                ("parent", C.c_void_p), ("child", C.c_void_p), ("face_flux", C.c_void_p)]
+
+
+class gamer_hierarchy_t(C.Structure):
+    _fields_ = [("n_levels", C.c_int32), ("reserved", C.c_int32),
+                ("levels", C.POINTER(gamer_level_t)), ("version", C.c_uint64)]
+
+
+class GamerError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True) -> C.CDLL:
+    """Load the CUDA library (building it first when sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_needed else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgamer_hydro.so not found at {path}; run __graft_entry__.build()")
+        L = C.CDLL(path)
+        H, vp, dp, ip = C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
+        hp = C.POINTER(gamer_hierarchy_t)
+        L.gamer_hydro_create.argtypes = [C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(H)]
+        L.gamer_hydro_destroy.argtypes = [H]
+        L.gamer_hydro_set_stream.argtypes = [H, vp]
+        L.gamer_hydro_set_parity.argtypes = [H, C.c_int, C.c_int]
+        L.gamer_hydro_get_parity.argtypes = [H, C.c_int, ip]
+        L.gamer_hydro_cfl_dt.argtypes = [H, hp, C.c_double, dp]
+        L.gamer_hydro_advance.argtypes = [H, hp, C.c_int, C.c_double]
+        L.gamer_hydro_fixup.argtypes = [H, hp, C.c_int, C.c_double]
+        L.gamer_hydro_advance_all.argtypes = [H, hp, C.c_double]
+        L.gamer_hydro_check.argtypes = [H, hp, dp, C.POINTER(C.c_int64)]
+        L.gamer_hydro_diagnose.argtypes = [H, hp, C.c_double, dp, dp, C.POINTER(C.c_int64)]
+        L.gamer_hydro_last_error.argtypes = [H]
+        L.gamer_hydro_last_error.restype = C.c_char_p
+        for name in EXPORTS:
+            if name != "gamer_hydro_last_error":
+                getattr(L, name).restype = C.c_int
+        _lib = L
+        return L
+
+
+def _check(h, code):
+    if code != GAMER_OK:
+        msg = load().gamer_hydro_last_error(h).decode()
+        raise GamerError(code, msg)
+
+
+# ------------------------------------------------ C functions, same names
+
+def gamer_hydro_create(gamma: float, limiter: int = GAMER_LIMITER_VANLEER, ghost_width: int = 3,
+                       precision: int = GAMER_FP32):
+    h = C.c_void_p()
+    _check(None, load().gamer_hydro_create(gamma, limiter, ghost_width, precision, C.byref(h)))
+    return h
+
+
+def gamer_hydro_destroy(h) -> None:
+    load().gamer_hydro_destroy(h)
+
+
+def gamer_hydro_set_stream(h, stream) -> None:
+    """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+    raw = None if stream is None else getattr(stream, "cuda_stream", stream)
+    _check(h, load().gamer_hydro_set_stream(h, C.c_void_p(raw) if raw else None))
+
+
+def gamer_hydro_set_parity(h, level: int, parity: int) -> None:
+    _check(h, load().gamer_hydro_set_parity(h, level, parity))
+
+
+def gamer_hydro_get_parity(h, level: int) -> int:
+    p = C.c_int()
+    _check(h, load().gamer_hydro_get_parity(h, level, C.byref(p)))
+    return p.value
+
+
+def gamer_hydro_cfl_dt(h, H, cfl: float) -> float:
+    dt = C.c_double()
+    _check(h, load().gamer_hydro_cfl_dt(h, H.struct(), cfl, C.byref(dt)))
+    return dt.value
+
+
+def gamer_hydro_advance(h, H, level: int, dt: float) -> None:
+    _check(h, load().gamer_hydro_advance(h, H.struct(), level, dt))
+
+
+def gamer_hydro_fixup(h, H, level: int, dt: float) -> None:
+    _check(h, load().gamer_hydro_fixup(h, H.struct(), level, dt))
+
+
+def gamer_hydro_advance_all(h, H, dt: float) -> None:
+    _check(h, load().gamer_hydro_advance_all(h, H.struct(), dt))
+
+
+def gamer_hydro_check(h, H):
+    sums = (C.c_double * 5)()
+    nb = C.c_int64()
+    _check(h, load().gamer_hydro_check(h, H.struct(), sums, C.byref(nb)))
+    return np.array(sums[:]), int(nb.value)
+
+
+def gamer_hydro_diagnose(h, H, cfl: float):
+    dt = C.c_double()
+    sums = (C.c_double * 5)()
+    nb = C.c_int64()
+    _check(h, load().gamer_hydro_diagnose(h, H.struct(), cfl, C.byref(dt), sums, C.byref(nb)))
+    return dt.value, np.array(sums[:]), int(nb.value)
+
+
+def gamer_hydro_last_error(h) -> str:
+    return load().gamer_hydro_last_error(h).decode()
+
+
+# ------------------------------------------------ device-side hierarchy
+
+_version_counter = [0]
+
+
+class DeviceHierarchy:
+    """A hierarchy snapshot on the device: maps as int32 tensors, per-level
+    state tensors u / u_out ([5, 8n, 8, 8, 8], float32 or float64), and the
+    C structs that point at them.  ``swap()`` exchanges u and u_out."""
+
+    def __init__(self, H, states, dtype, device="cuda", with_flux=False):
+        import torch
+        self.torch = torch
+        self.H = H
+        self.dtype = dtype
+        self.device = torch.device(device)
+        n = H.n_levels
+        self.u = [torch.as_tensor(np.ascontiguousarray(s), dtype=dtype).to(self.device) for s in states]
+        self.u_out = [torch.empty_like(x) for x in self.u]
+        self.nbr = [torch.as_tensor(np.ascontiguousarray(lv.nbr, dtype=np.int32)).to(self.device)
+                    for lv in H.levels]
+        self.parent = [None if lv.parent is None else
+                       torch.as_tensor(np.ascontiguousarray(lv.parent, dtype=np.int32)).to(self.device)
+                       for lv in H.levels]
+        self.child = [None if lv.child is None else
+                      torch.as_tensor(np.ascontiguousarray(lv.child, dtype=np.int32)).to(self.device)
+                      for lv in H.levels]
+        self.flux = [torch.zeros((lv.n_groups, 3, 3, 5, 16, 16), dtype=dtype, device=self.device)
+                     if (with_flux and n > 1) else None for lv in H.levels]
+        _version_counter[0] += 1
+        self.version = _version_counter[0]
+        self._levels = (gamer_level_t * n)()
+        self._hier = gamer_hierarchy_t()
+        self._refresh()
+
+    @staticmethod
+    def _ptr(t):
+        return None if t is None or t.numel() == 0 else t.data_ptr()
+
+    def _refresh(self):
+        for l, lv in enumerate(self.H.levels):
+            s = self._levels[l]
+            s.n_groups = lv.n_groups
+            s.dh = lv.dh
+            s.u = self._ptr(self.u[l])
+            s.u_out = self._ptr(self.u_out[l])
+            s.nbr = self._ptr(self.nbr[l])
+            s.parent = self._ptr(self.parent[l]) if l > 0 else None
+            s.child = self._ptr(self.child[l]) if l + 1 < self.H.n_levels else None
+            s.face_flux = self._ptr(self.flux[l])
+        self._hier.n_levels = self.H.n_levels
+        self._hier.levels = self._levels
+        self._hier.version = self.version
+
+    def struct(self):
+        return C.byref(self._hier)
+
+    def swap(self):
+        self.u, self.u_out = self.u_out, self.u
+        self._refresh()
+
+    def states(self):
+        return [x.detach().double().cpu().numpy() for x in self.u]
+
+
+class Solver:
+    """Convenience wrapper: one handle + the calls of one step."""
+
+    def __init__(self, gamma=5.0 / 3.0, limiter=GAMER_LIMITER_VANLEER, precision=GAMER_FP32, stream=None):
+        self.h = gamer_hydro_create(gamma, limiter, 3, precision)
+        if stream is not None:
+            gamer_hydro_set_stream(self.h, stream)
+
+    def close(self):
+        if self.h:
+            gamer_hydro_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, D: DeviceHierarchy, dt: float):
+        """advance_all + swap."""
+        gamer_hydro_advance_all(self.h, D, dt)
+        D.swap()
+
+    def run(self, D: DeviceHierarchy, cfl: float, n_calls: int):
+        """n_calls sweep sets; dt from Eq. CFL before each xyz call, held for
+        the following zyx call.  Returns the dt list."""
+        dts, dt = [], None
+        for c in range(n_calls):
+            if gamer_hydro_get_parity(self.h, 0) == 0 or dt is None:
+                dt = gamer_hydro_cfl_dt(self.h, D, cfl)
+            self.step(D, dt)
+            dts.append(dt)
+        return dts

@@ -1,0 +1,260 @@
+// aux_kernels.cu -- coarse-fine fix-up and diagnostics (CFL maxima,
+// conservation sums, positivity count), for both element types.
+#include "common.cuh"
+#include "internal.h"
+
+namespace gh {
+
+// ------------------------------------------------------------ fix-up
+
+// One thread block of 512 threads per listed coarse patch P (one thread per
+// cell of the 8^3 patch).  A refined patch (child >= 0) gets the mean of
+// its 8 children per cell (restriction, Sec. 2.1 step 3); a leaf patch gets
+// the coarse-fine flux correction on every face whose same-level neighbour
+// patch is refined: the coarse flux is replaced by the mean of the 4 fine
+// fluxes of that face (Berger-Colella), faces in the order x-, x+, y-, y+,
+// z-, z+.
+template <typename T>
+__global__ void __launch_bounds__(512) k_fixup(const FixArgs<T> a) {
+    const int P = a.list[blockIdx.x];
+    const int g = P >> 3, lp = P & 7;
+    const int pc[3] = {lp & 1, (lp >> 1) & 1, (lp >> 2) & 1};
+    const int t = threadIdx.x;
+    const int ci[3] = {t & 7, (t >> 3) & 7, t >> 6};
+    const size_t vsc = (size_t)a.n_c * 8 * 512, vsf = (size_t)a.n_f * 8 * 512;
+    const int X = PS * pc[0] + ci[0], Y = PS * pc[1] + ci[1], Z = PS * pc[2] + ci[2];
+    const size_t co = cell_offset(g, X, Y, Z);
+    const int gf = a.child[P];
+    if (gf >= 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const T* f = a.uf + v * vsf;
+            T s = T(0);
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+                for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 2; ++dx)
+                        s = s + f[cell_offset(gf, 2 * ci[0] + dx, 2 * ci[1] + dy, 2 * ci[2] + dz)];
+            a.uc[v * vsc + co] = T(0.125) * s;
+        }
+        return;
+    }
+    T val[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) val[v] = a.uc[v * vsc + co];
+    bool touched = false;
+    for (int ax = 0; ax < 3; ++ax) {
+        const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
+        for (int s = -1; s <= 1; s += 2) {
+            if (ci[ax] != (s > 0 ? PS - 1 : 0)) continue;
+            int q[3] = {pc[0], pc[1], pc[2]};
+            q[ax] += s;
+            int gq = g;
+            if (q[ax] < 0 || q[ax] > 1) {
+                int e[3] = {0, 0, 0};
+                e[ax] = s;
+                gq = a.nbr[(size_t)g * 26 + dir_index(e[0], e[1], e[2])];
+                q[ax] = q[ax] < 0 ? 1 : 0;
+            }
+            if (gq < 0) continue;
+            const int gfq = a.child[8 * gq + (q[2] * 2 + q[1]) * 2 + q[0]];
+            if (gfq < 0) continue;
+            const int plane_c = s > 0 ? pc[ax] + 1 : pc[ax];
+            const int plane_f = s > 0 ? 0 : 2;
+            const int b1 = ci[t1], b2 = ci[t2];
+            const int T1 = PS * pc[t1] + b1, T2 = PS * pc[t2] + b2;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const T Gc = a.flux_c[((((size_t)g * 3 + ax) * 3 + plane_c) * NV + v) * 256 + T2 * GS + T1];
+                const T* ff = a.flux_f + ((((size_t)gfq * 3 + ax) * 3 + plane_f) * NV + v) * 256;
+                const T Gf = T(0.25) * (((ff[(2 * b2) * GS + 2 * b1] + ff[(2 * b2) * GS + 2 * b1 + 1]) +
+                                         ff[(2 * b2 + 1) * GS + 2 * b1]) + ff[(2 * b2 + 1) * GS + 2 * b1 + 1]);
+                if (s > 0) val[v] = val[v] + a.lam * (Gc - Gf);
+                else val[v] = val[v] - a.lam * (Gc - Gf);
+            }
+            touched = true;
+        }
+    }
+    if (touched) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) a.uc[v * vsc + co] = val[v];
+    }
+}
+
+template <typename T>
+cudaError_t launch_fixup(const FixArgs<T>& a, int n_list, cudaStream_t st) {
+    if (n_list <= 0) return cudaSuccess;
+    k_fixup<T><<<n_list, 512, 0, st>>>(a);
+    return cudaGetLastError();
+}
+template cudaError_t launch_fixup<float>(const FixArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_fixup<double>(const FixArgs<double>&, int, cudaStream_t);
+
+// ------------------------------------------------------------ diagnostics
+
+// Signal speed c_s + max(|vx|,|vy|,|vz|) of one cell (denominator of Eq.
+// CFL) and its pressure.  FP64: the plain order of operations; FP32: the
+// fast single-precision forms of the FP32 path.
+__device__ __forceinline__ void speed_pressure(const double u[NV], double g, double gm1, double& s,
+                                               double& P) {
+    const double rho = u[0];
+    const double vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho;
+    const double eps = u[4] - (0.5 * rho) * ((vx * vx + vy * vy) + vz * vz);
+    P = gm1 * eps;
+    const double cs = sqrt((g * fmax(P, 0.0)) / rho);
+    s = cs + fmax(fmax(fabs(vx), fabs(vy)), fabs(vz));
+}
+__device__ __forceinline__ void speed_pressure(const float u[NV], float g, float gm1, float& s,
+                                               float& P) {
+    const float ri = __fdividef(1.0f, u[0]);
+    const float m2 = fmaf(u[1], u[1], fmaf(u[2], u[2], u[3] * u[3]));
+    P = gm1 * fmaf(-0.5f * ri, m2, u[4]);
+    const float cs = sqrtf(g * fmaxf(P, 0.0f) * ri);
+    s = cs + fmaxf(fmaxf(fabsf(u[1]), fabsf(u[2])), fabsf(u[3])) * ri;
+}
+
+// Error-free accumulation for the FP32 path: a double-float (hi, lo) pair
+// per thread (Knuth's two-sum), converted to FP64 before any cross-thread
+// combination.  The FP64 path accumulates in FP64 directly.
+struct Acc32 {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float s = hi + x;
+        const float bb = s - hi;
+        const float err = (hi - (s - bb)) + (x - bb);
+        hi = s;
+        lo += err;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+struct Acc64 {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <typename T> struct AccOf;
+template <> struct AccOf<float> { using type = Acc32; };
+template <> struct AccOf<double> { using type = Acc64; };
+
+constexpr int NT_DIAG = 256;
+
+// One block per patch group (of any level): exact per-group maximum of the
+// signal speed over all cells, leaf-cell sums of the 5 conserved variables
+// (fixed assignment of cells to threads, fixed tree) and the count of leaf
+// cells with rho <= 0, P <= 0 or a non-finite variable.
+template <typename T>
+__global__ void __launch_bounds__(NT_DIAG) k_diag(const DiagArgs<T> a) {
+    using Acc = typename AccOf<T>::type;
+    const int item = blockIdx.x;
+    int l = 0;
+    while (l + 1 < a.n_levels && item >= a.lv[l + 1].item0) ++l;
+    const DiagLevel<T>& L = a.lv[l];
+    const int g = item - L.item0;
+    const size_t vstride = (size_t)L.n_groups * 8 * 512;
+    const T* base = L.u + ((size_t)g << 12);
+    unsigned long long smax = 0ull;
+    Acc acc[NV];
+    int bad = 0;
+    for (int i = threadIdx.x; i < CELLS_PG; i += NT_DIAG) {
+        const int patch = i >> 9;
+        const bool leaf = L.child == nullptr || L.child[8 * g + patch] < 0;
+        T u[NV];
+        bool finite = true;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            u[v] = base[v * vstride + i];
+            finite = finite && isfinite(u[v]);
+        }
+        T s, P;
+        speed_pressure(u, a.gamma, a.gm1, s, P);
+        const unsigned long long sb = (unsigned long long)__double_as_longlong((double)s);
+        smax = sb > smax ? sb : smax;
+        if (leaf) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) acc[v].add(u[v]);
+            if (!finite || !(u[0] > T(0)) || !(P > T(0))) ++bad;
+        }
+    }
+    __shared__ double s_sum[NV][NT_DIAG];
+    __shared__ unsigned long long s_max[NT_DIAG];
+    __shared__ int s_bad[NT_DIAG];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s_sum[v][threadIdx.x] = acc[v].value();
+    s_max[threadIdx.x] = smax;
+    s_bad[threadIdx.x] = bad;
+    __syncthreads();
+    for (int w = NT_DIAG / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) s_sum[v][threadIdx.x] += s_sum[v][threadIdx.x + w];
+            s_max[threadIdx.x] = max(s_max[threadIdx.x], s_max[threadIdx.x + w]);
+            s_bad[threadIdx.x] += s_bad[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        a.pg_max[item] = s_max[0];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) a.pg_sum[(size_t)item * NV + v] = s_sum[v][0];
+        a.pg_bad[item] = s_bad[0];
+    }
+}
+
+// One block per level: combine the per-group results of the level in a
+// fixed order (strided partials, then a fixed tree).
+constexpr int NT_FIN = 256;
+template <typename T>
+__global__ void __launch_bounds__(NT_FIN) k_diag_final(const DiagArgs<T> a) {
+    const int l = blockIdx.x;
+    const int i0 = a.lv[l].item0, n = a.lv[l].n_groups;
+    double sum[NV] = {0, 0, 0, 0, 0};
+    unsigned long long m = 0ull;
+    long long bad = 0;
+    for (int i = threadIdx.x; i < n; i += NT_FIN) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sum[v] += a.pg_sum[(size_t)(i0 + i) * NV + v];
+        m = max(m, a.pg_max[i0 + i]);
+        bad += a.pg_bad[i0 + i];
+    }
+    __shared__ double s_sum[NV][NT_FIN];
+    __shared__ unsigned long long s_max[NT_FIN];
+    __shared__ long long s_bad[NT_FIN];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s_sum[v][threadIdx.x] = sum[v];
+    s_max[threadIdx.x] = m;
+    s_bad[threadIdx.x] = bad;
+    __syncthreads();
+    for (int w = NT_FIN / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) s_sum[v][threadIdx.x] += s_sum[v][threadIdx.x + w];
+            s_max[threadIdx.x] = max(s_max[threadIdx.x], s_max[threadIdx.x + w]);
+            s_bad[threadIdx.x] += s_bad[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        DiagOut* o = a.out + l;
+        o->smax_bits = s_max[0];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) o->sum[v] = s_sum[v][0];
+        o->n_bad = s_bad[0];
+    }
+}
+
+template <typename T>
+cudaError_t launch_diag(const DiagArgs<T>& a, int total, cudaStream_t st) {
+    if (total > 0) {
+        k_diag<T><<<total, NT_DIAG, 0, st>>>(a);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    k_diag_final<T><<<a.n_levels, NT_FIN, 0, st>>>(a);
+    return cudaGetLastError();
+}
+template cudaError_t launch_diag<float>(const DiagArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_diag<double>(const DiagArgs<double>&, int, cudaStream_t);
+
+}  // namespace gh

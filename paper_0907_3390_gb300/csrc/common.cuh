@@ -1,0 +1,197 @@
+// common.cuh -- device-side building blocks shared by the FP32 and FP64
+// kernels: sizes, kernel argument structs, patch indexing, the ghost-zone
+// gather (same-level copy, outflow clamp, Min-Mod interpolation from the
+// coarser level) and the diagnostic helpers.
+//
+// Geometry (Sec. 3.1): a patch is 8^3 cells, a patch group the 2x2x2 oct of
+// sibling patches (16^3 interior cells), padded by NG = 3 ghost cells per
+// side for the seven-point stencil (Sec. 2.2) into a 22^3 block.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gh {
+
+constexpr int NV = 5;      // rho, mx, my, mz, e
+constexpr int PS = 8;      // patch size
+constexpr int GS = 16;     // patch-group size
+constexpr int NG = 3;      // ghost cells per side
+constexpr int PD = 22;     // padded size
+constexpr int MAXLEV = 16; // levels per launch
+constexpr int CELLS_PG = GS * GS * GS;          // 4096
+constexpr int FLUX_PG = 3 * 3 * NV * GS * GS;   // face-flux values per group
+
+// One level as a kernel sees it.  All pointers are device memory.
+template <typename T>
+struct LevelArgs {
+    const T* u;         // [5][8n][8][8][8] pre-step state
+    T* u_out;           // post-step state
+    const int* nbr;     // [n][26]
+    T* flux;            // [n][3][3][5][16][16] or nullptr
+    const int* parent;  // [n] patch index on level-1, nullptr on level 0
+    const T* uc;        // level-1 pre-step state (coarse ghosts)
+    const int* nbrc;    // level-1 map
+    int n_groups;
+    int n_groups_c;
+    int item0;          // first work item of this level in a multi-level launch
+    int pad_;
+    T lam;              // dt / dh of this level
+};
+
+template <typename T>
+struct SweepArgs {
+    LevelArgs<T> lv[MAXLEV];
+    int n_levels;
+    int total;          // work items (patch groups) over all levels
+    int* queue;         // device work-queue counter, zero before launch
+    T gamma;
+    T gm1;              // gamma - 1, formed once on the host in FP64
+};
+
+__host__ __device__ __forceinline__ int dir_index(int dx, int dy, int dz) {
+    int d = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+    return d < 13 ? d : d - 1;
+}
+
+// Offset of cell (x,y,z), 0 <= x,y,z < 16, of group g inside one variable's
+// array of the patch layout.
+__device__ __forceinline__ size_t cell_offset(int g, int x, int y, int z) {
+    int patch = (((z >> 3) << 1 | (y >> 3)) << 1) | (x >> 3);
+    return ((size_t)(8 * g + patch) << 9) + (size_t)((((z & 7) << 3) | (y & 7)) << 3 | (x & 7));
+}
+
+// Region table of one group: for each of the 27 regions r = (oz+1)*9 +
+// (oy+1)*3 + (ox+1) around it, the source group after outflow clamping
+// (axes whose face neighbour is -2 are clamped into the group first), and
+// the clamp mask (bit a set = clamp axis a).  src = -1: coarse region.
+// Called by 27 threads.
+__device__ __forceinline__ void region_entry(const int* __restrict__ nbr, int g, int r,
+                                             int* s_src, int* s_mask) {
+    int o[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
+    int mask = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (o[a] != 0) {
+            int e[3] = {0, 0, 0};
+            e[a] = o[a];
+            if (nbr[(size_t)g * 26 + dir_index(e[0], e[1], e[2])] == -2) {
+                mask |= 1 << a;
+                o[a] = 0;
+            }
+        }
+    }
+    int src = g;
+    if (o[0] | o[1] | o[2]) src = nbr[(size_t)g * 26 + dir_index(o[0], o[1], o[2])];
+    s_src[r] = src;
+    s_mask[r] = mask;
+}
+
+__device__ __forceinline__ int region_of(int c) { return c < 0 ? -1 : (c >= GS ? 1 : 0); }
+
+// Resolve a group-local position (-16 <= c < 32) through a region table:
+// returns the source group (or -1 / < -1) and rewrites c into it.
+__device__ __forceinline__ int resolve(const int* s_src, const int* s_mask, int& x, int& y, int& z) {
+    int ox = region_of(x), oy = region_of(y), oz = region_of(z);
+    int r = (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1);
+    int m = s_mask[r];
+    x = (m & 1) ? min(max(x, 0), GS - 1) : x - GS * ox;
+    y = (m & 2) ? min(max(y, 0), GS - 1) : y - GS * oy;
+    z = (m & 4) ? min(max(z, 0), GS - 1) : z - GS * oz;
+    return s_src[r];
+}
+
+template <typename T>
+__device__ __forceinline__ T minmod_slope(T l, T c, T r) {
+    T a = c - l, b = r - c;
+    if (a * b > T(0)) {
+        T m = fmin(fabs(a), fabs(b));
+        return a > T(0) ? m : -m;
+    }
+    return T(0);
+}
+
+// Conservative linear interpolation with the Min-Mod limiter (Sec. 2.1
+// refinement step, Sec. 2.2 ghost zones) of the fine ghost cell at
+// group-local (x,y,z) of a group whose parent patch has local position
+// (px,py,pz) in coarse group gc.  Coarse data: the coarse level's pre-step
+// state uc, resolved through the coarse region table.  Writes NV values.
+template <typename T>
+__device__ __forceinline__ void prolong(const T* __restrict__ uc, size_t vstride_c,
+                                        const int* s_csrc, const int* s_cmask, int px, int py,
+                                        int pz, int x, int y, int z, T out[NV]) {
+    const int cx = PS * px + (x >> 1), cy = PS * py + (y >> 1), cz = PS * pz + (z >> 1);
+    const T sx = (x & 1) ? T(1) : T(-1);
+    const T sy = (y & 1) ? T(1) : T(-1);
+    const T sz = (z & 1) ? T(1) : T(-1);
+    size_t off[7];
+    const int dd[7][3] = {{0, 0, 0}, {-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        int a = cx + dd[q][0], b = cy + dd[q][1], c = cz + dd[q][2];
+        int s = resolve(s_csrc, s_cmask, a, b, c);
+        off[q] = cell_offset(s < 0 ? 0 : s, a, b, c);   // s < 0 cannot pass host validation
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const T* p = uc + v * vstride_c;
+        T U = p[off[0]];
+        T Sx = minmod_slope(p[off[1]], U, p[off[2]]);
+        T Sy = minmod_slope(p[off[3]], U, p[off[4]]);
+        T Sz = minmod_slope(p[off[5]], U, p[off[6]]);
+        T t = (sx * Sx + sy * Sy) + sz * Sz;
+        out[v] = U + T(0.25) * t;
+    }
+}
+
+// Fill the padded block blk (pitches XP along x, PD rows along y, PD
+// planes along z, VS per variable) of group g on level L by all threads of
+// the block.  s_src/s_mask: region table of g; s_csrc/s_cmask: region table
+// of the parent's coarse group (only read where a region is -1).
+template <typename T, int XP, int NT>
+__device__ __forceinline__ void gather_block(T* blk, size_t VS, const LevelArgs<T>& L, int g,
+                                             const int* s_src, const int* s_mask,
+                                             const int* s_csrc, const int* s_cmask, int ppx,
+                                             int ppy, int ppz) {
+    const size_t vstride = (size_t)L.n_groups * 8 * 512;
+    const size_t vstride_c = (size_t)L.n_groups_c * 8 * 512;
+    for (int i = threadIdx.x; i < PD * PD * PD; i += NT) {
+        int xp = i % PD, t = i / PD;
+        int yp = t % PD, zp = t / PD;
+        int x = xp - NG, y = yp - NG, z = zp - NG;
+        int s = resolve(s_src, s_mask, x, y, z);
+        T* d = blk + ((size_t)zp * PD + yp) * XP + xp;
+        if (s >= 0) {
+            const T* p = L.u + cell_offset(s, x, y, z);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) d[v * VS] = p[v * vstride];
+        } else {
+            T val[NV];
+            prolong<T>(L.uc, vstride_c, s_csrc, s_cmask, ppx, ppy, ppz, xp - NG, yp - NG, zp - NG,
+                       val);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) d[v * VS] = val[v];
+        }
+    }
+}
+
+// Build the region tables of group g (and of its parent's coarse group when
+// the level has a parent map).  Threads 0..26 and 32..58 of the block.
+template <typename T>
+__device__ __forceinline__ void build_tables(const LevelArgs<T>& L, int g, int* s_src, int* s_mask,
+                                             int* s_csrc, int* s_cmask, int* s_par) {
+    int t = threadIdx.x;
+    if (t < 27) region_entry(L.nbr, g, t, s_src, s_mask);
+    if (L.parent != nullptr) {
+        int P = L.parent[g];
+        if (t >= 32 && t < 59) region_entry(L.nbrc, P >> 3, t - 32, s_csrc, s_cmask);
+        if (t == 0) s_par[0] = P;
+    } else if (t == 0) {
+        s_par[0] = -1;
+    }
+}
+
+// Exact-order maximum of positive doubles through their bit patterns.
+__device__ __forceinline__ void atomic_max_pos(unsigned long long* addr, double v) {
+    atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+}  // namespace gh

@@ -1,0 +1,592 @@
+// hydro_api.cu -- the C ABI of include/gamer_hydro.h: handle, validation of
+// hierarchy snapshots, scratch management, launch sequencing, CUDA-graph
+// replay of whole steps, and error reporting.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/gamer_hydro.h"
+#include "internal.h"
+
+using namespace gh;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    uint64_t last_use = 0;
+};
+
+struct LevelCache {
+    int n_groups = 0;
+    double dh = 0.0;
+    std::vector<int> fix_list;    // coarse patches visited by the fix-up of this level
+    int* d_fix_list = nullptr;
+    void* own_flux = nullptr;     // handle-owned face fluxes when the caller gives none
+};
+
+}  // namespace
+
+struct gamer_hydro_s {
+    double gamma = 5.0 / 3.0;
+    int limiter = GAMER_LIMITER_VANLEER;
+    int precision = GAMER_FP32;
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    int parity[32] = {0};
+    std::string err;
+
+    // hierarchy cache (maps are validated once per version)
+    bool have_version = false;
+    uint64_t version = 0;
+    int n_levels = 0;
+    std::vector<LevelCache> lv;
+    int total_groups = 0;
+
+    // scratch
+    int* d_queue = nullptr;
+    unsigned long long* d_pg_max = nullptr;
+    double* d_pg_sum = nullptr;
+    int* d_pg_bad = nullptr;
+    DiagOut* d_out = nullptr;
+    DiagOut* h_out = nullptr;     // pinned
+    int diag_cap = 0;
+    double* d_stage = nullptr;
+    int stage_groups = 0;
+
+    // tuning
+    int sweep_threads = 512;
+    int f64_chunk = 2048;
+
+    // graphs of advance_all, keyed by the launch arguments
+    std::map<std::string, GraphEntry> graphs;
+    uint64_t use_clock = 0;
+    double* d_dt = nullptr;       // device copy of dt read by graph replays
+};
+
+namespace {
+
+int fail(gamer_hydro_t h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(gamer_hydro_t h, cudaError_t e, const char* what) {
+    return fail(h, GAMER_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                                   \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);      \
+    } while (0)
+
+int floordiv(int a, int b) {
+    int q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+    return q;
+}
+
+// Host mirror of the device region resolution: source group of a position
+// (in patch units relative to group g) after the outflow clamp.  Returns
+// the group index (>= 0), -1 (coarse) or another negative map value.
+int resolve_patch(const std::vector<int>& nbr, int g, int q[3]) {
+    int o[3];
+    for (int a = 0; a < 3; ++a) {
+        o[a] = floordiv(q[a], 2);
+        if (o[a] != 0) {
+            int e[3] = {0, 0, 0};
+            e[a] = o[a];
+            if (nbr[(size_t)g * 26 + dir_index(e[0], e[1], e[2])] == -2) {
+                q[a] = q[a] < 0 ? 0 : 1;
+                o[a] = 0;
+            }
+        }
+    }
+    for (int a = 0; a < 3; ++a) q[a] -= 2 * o[a];
+    if (!(o[0] | o[1] | o[2])) return g;
+    return nbr[(size_t)g * 26 + dir_index(o[0], o[1], o[2])];
+}
+
+template <typename T>
+void fill_level(LevelArgs<T>& a, const gamer_level_t* L, int l, const gamer_hydro_s* h,
+                double dt) {
+    const gamer_level_t& c = L[l];
+    a.u = static_cast<const T*>(c.u);
+    a.u_out = static_cast<T*>(c.u_out);
+    a.nbr = c.nbr;
+    a.flux = static_cast<T*>(c.face_flux ? c.face_flux : h->lv[l].own_flux);
+    if (h->n_levels == 1) a.flux = nullptr;
+    a.parent = l > 0 ? c.parent : nullptr;
+    a.uc = l > 0 ? static_cast<const T*>(L[l - 1].u) : nullptr;
+    a.nbrc = l > 0 ? L[l - 1].nbr : nullptr;
+    a.n_groups = c.n_groups;
+    a.n_groups_c = l > 0 ? L[l - 1].n_groups : 0;
+    a.item0 = 0;
+    a.pad_ = 0;
+    a.lam = (T)(dt / c.dh);
+}
+
+size_t elem_size(const gamer_hydro_s* h) { return h->precision == GAMER_FP64 ? 8 : 4; }
+
+int ensure_diag(gamer_hydro_t h, int total) {
+    if (total <= h->diag_cap && h->d_out) return GAMER_OK;
+    cudaFree(h->d_pg_max);
+    cudaFree(h->d_pg_sum);
+    cudaFree(h->d_pg_bad);
+    h->d_pg_max = nullptr; h->d_pg_sum = nullptr; h->d_pg_bad = nullptr;
+    int cap = std::max(total, 1);
+    CK(h, cudaMalloc(&h->d_pg_max, sizeof(unsigned long long) * cap));
+    CK(h, cudaMalloc(&h->d_pg_sum, sizeof(double) * NV * cap));
+    CK(h, cudaMalloc(&h->d_pg_bad, sizeof(int) * cap));
+    if (!h->d_out) {
+        CK(h, cudaMalloc(&h->d_out, sizeof(DiagOut) * MAXLEV));
+        CK(h, cudaMallocHost(&h->h_out, sizeof(DiagOut) * MAXLEV));
+    }
+    h->diag_cap = cap;
+    return GAMER_OK;
+}
+
+void drop_graphs(gamer_hydro_t h) {
+    for (auto& kv : h->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    h->graphs.clear();
+}
+
+void drop_hierarchy(gamer_hydro_t h) {
+    for (auto& c : h->lv) {
+        cudaFree(c.d_fix_list);
+        cudaFree(c.own_flux);
+    }
+    h->lv.clear();
+    h->have_version = false;
+    drop_graphs(h);
+}
+
+// Validate a hierarchy snapshot (once per version) and build the fix-up
+// work lists.  Maps are copied to the host; this synchronises the device.
+int prepare(gamer_hydro_t h, const gamer_hierarchy_t* H) {
+    if (!H || !H->levels) return fail(h, GAMER_ERR_ARG, "hierarchy is NULL");
+    if (H->n_levels < 1 || H->n_levels > MAXLEV)
+        return fail(h, GAMER_ERR_ARG, "n_levels must be in [1, 16]");
+    if (h->have_version && h->version == H->version && h->n_levels == H->n_levels) {
+        for (int l = 0; l < H->n_levels; ++l)
+            if (H->levels[l].n_groups != h->lv[l].n_groups || H->levels[l].dh != h->lv[l].dh)
+                return fail(h, GAMER_ERR_STATE, "maps changed without a new hierarchy version");
+        return GAMER_OK;
+    }
+    drop_hierarchy(h);
+    const int n = H->n_levels;
+    std::vector<std::vector<int>> nbr(n), parent(n), child(n);
+    int total = 0;
+    for (int l = 0; l < n; ++l) {
+        const gamer_level_t& L = H->levels[l];
+        if (L.n_groups < 0) return fail(h, GAMER_ERR_ARG, "negative n_groups");
+        if (!(L.dh > 0.0)) return fail(h, GAMER_ERR_ARG, "dh must be positive");
+        if (L.n_groups > 0 && (!L.u || !L.u_out || !L.nbr))
+            return fail(h, GAMER_ERR_ARG, "u, u_out and nbr are required");
+        if (L.n_groups > 0 && L.u == L.u_out)
+            return fail(h, GAMER_ERR_ARG, "u_out must not alias u");
+        total += L.n_groups;
+        nbr[l].resize((size_t)L.n_groups * 26);
+        if (L.n_groups > 0)
+            CK(h, cudaMemcpy(nbr[l].data(), L.nbr, sizeof(int) * nbr[l].size(), cudaMemcpyDeviceToHost));
+        if (l > 0 && L.n_groups > 0) {
+            if (!L.parent) return fail(h, GAMER_ERR_MAP, "parent map required above level 0");
+            parent[l].resize(L.n_groups);
+            CK(h, cudaMemcpy(parent[l].data(), L.parent, sizeof(int) * L.n_groups, cudaMemcpyDeviceToHost));
+        }
+        if (l + 1 < n && L.n_groups > 0) {
+            if (!L.child) return fail(h, GAMER_ERR_MAP, "child map required below the finest level");
+            child[l].resize((size_t)8 * L.n_groups);
+            CK(h, cudaMemcpy(child[l].data(), L.child, sizeof(int) * child[l].size(), cudaMemcpyDeviceToHost));
+        }
+    }
+    for (int l = 0; l < n; ++l) {
+        const int ng = H->levels[l].n_groups;
+        for (int v : nbr[l]) {
+            if (v >= ng || v < -2) return fail(h, GAMER_ERR_MAP, "nbr entry out of range on level " + std::to_string(l));
+            if (v == -1 && l == 0) return fail(h, GAMER_ERR_MAP, "coarse (-1) neighbour on level 0");
+        }
+        // every ghost region must resolve (after the outflow clamp) to a
+        // same-level group, or to the coarser level above level 0
+        for (int g = 0; g < ng; ++g)
+            for (int r = 0; r < 27; ++r) {
+                if (r == 13) continue;
+                int o[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
+                for (int a = 0; a < 3; ++a) {
+                    if (o[a] == 0) continue;
+                    int e[3] = {0, 0, 0};
+                    e[a] = o[a];
+                    if (nbr[l][(size_t)g * 26 + dir_index(e[0], e[1], e[2])] == -2) o[a] = 0;
+                }
+                const int src = (o[0] | o[1] | o[2]) ? nbr[l][(size_t)g * 26 + dir_index(o[0], o[1], o[2])] : g;
+                if (src >= 0 || (src == -1 && l > 0)) continue;
+                return fail(h, GAMER_ERR_MAP, "ghost region of group " + std::to_string(g) + " on level " +
+                                                  std::to_string(l) + " does not resolve");
+            }
+        if (l > 0) {
+            const int nc = H->levels[l - 1].n_groups;
+            for (int g = 0; g < ng; ++g) {
+                int P = parent[l][g];
+                if (P < 0 || P >= 8 * nc) return fail(h, GAMER_ERR_MAP, "parent out of range on level " + std::to_string(l));
+                if (child[l - 1][P] != g) return fail(h, GAMER_ERR_MAP, "child[parent[g]] != g on level " + std::to_string(l));
+                // proper nesting: the 26 neighbours of the parent patch exist
+                bool needs = false;
+                for (int d = 0; d < 26; ++d) needs |= nbr[l][(size_t)g * 26 + d] == -1;
+                if (!needs) continue;
+                const int gc = P >> 3, lp = P & 7;
+                for (int dz = -1; dz <= 1; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            int q[3] = {(lp & 1) + dx, ((lp >> 1) & 1) + dy, ((lp >> 2) & 1) + dz};
+                            if (resolve_patch(nbr[l - 1], gc, q) < 0)
+                                return fail(h, GAMER_ERR_MAP, "proper nesting violated on level " + std::to_string(l));
+                        }
+            }
+        }
+        if (l + 1 < n) {
+            const int nf = H->levels[l + 1].n_groups;
+            for (int c : child[l])
+                if (c < -1 || c >= nf) return fail(h, GAMER_ERR_MAP, "child entry out of range on level " + std::to_string(l));
+        }
+    }
+    h->lv.assign(n, LevelCache());
+    for (int l = 0; l < n; ++l) {
+        LevelCache& c = h->lv[l];
+        c.n_groups = H->levels[l].n_groups;
+        c.dh = H->levels[l].dh;
+        if (n > 1 && !H->levels[l].face_flux && c.n_groups > 0)
+            CK(h, cudaMalloc(&c.own_flux, (size_t)c.n_groups * FLUX_PG * elem_size(h)));
+        if (l + 1 < n) {
+            for (int P = 0; P < 8 * c.n_groups; ++P) {
+                bool take = child[l][P] >= 0;
+                if (!take) {
+                    const int g = P >> 3, lp = P & 7;
+                    for (int ax = 0; ax < 3 && !take; ++ax)
+                        for (int s = -1; s <= 1 && !take; s += 2) {
+                            int q[3] = {lp & 1, (lp >> 1) & 1, (lp >> 2) & 1};
+                            q[ax] += s;
+                            int gq = g;
+                            if (q[ax] < 0 || q[ax] > 1) {
+                                int e[3] = {0, 0, 0};
+                                e[ax] = s;
+                                gq = nbr[l][(size_t)g * 26 + dir_index(e[0], e[1], e[2])];
+                                q[ax] = q[ax] < 0 ? 1 : 0;
+                            }
+                            if (gq >= 0 && child[l][8 * gq + (q[2] * 2 + q[1]) * 2 + q[0]] >= 0) take = true;
+                        }
+                }
+                if (take) c.fix_list.push_back(P);
+            }
+            if (!c.fix_list.empty()) {
+                CK(h, cudaMalloc(&c.d_fix_list, sizeof(int) * c.fix_list.size()));
+                CK(h, cudaMemcpy(c.d_fix_list, c.fix_list.data(), sizeof(int) * c.fix_list.size(),
+                                 cudaMemcpyHostToDevice));
+            }
+        }
+    }
+    h->n_levels = n;
+    h->total_groups = total;
+    h->version = H->version;
+    h->have_version = true;
+    return ensure_diag(h, total);
+}
+
+int check_level_arg(gamer_hydro_t h, const gamer_hierarchy_t* H, int level) {
+    if (level < 0 || level >= H->n_levels) return fail(h, GAMER_ERR_ARG, "level out of range");
+    return GAMER_OK;
+}
+
+int advance_level_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, int l, double dt, int order) {
+    const gamer_level_t* L = H->levels;
+    if (L[l].n_groups == 0) return GAMER_OK;
+    if (h->precision == GAMER_FP32) {
+        SweepArgs<float> a;
+        memset(&a, 0, sizeof(a));
+        fill_level<float>(a.lv[0], L, l, h, dt);
+        a.n_levels = 1;
+        a.total = L[l].n_groups;
+        a.queue = h->d_queue;
+        a.gamma = (float)h->gamma;
+        a.gm1 = (float)(h->gamma - 1.0);
+        CK(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), h->stream));
+        const int grid = std::min(a.total, h->sm_count);
+        CK(h, launch_sweep_f32(a, order, h->limiter, h->sweep_threads, grid, h->stream));
+    } else {
+        LevelArgs<double> a;
+        memset(&a, 0, sizeof(a));
+        fill_level<double>(a, L, l, h, dt);
+        const int chunk = std::min(h->f64_chunk, L[l].n_groups);
+        if (h->stage_groups < chunk) {
+            cudaFree(h->d_stage);
+            h->d_stage = nullptr;
+            CK(h, cudaMalloc(&h->d_stage, stage_f64_bytes_per_group() * chunk));
+            h->stage_groups = chunk;
+        }
+        for (int g0 = 0; g0 < L[l].n_groups; g0 += chunk) {
+            const int cnt = std::min(chunk, L[l].n_groups - g0);
+            CK(h, launch_pg_f64(a, g0, cnt, order, h->limiter, h->gamma, h->gamma - 1.0, h->d_stage,
+                                h->stream));
+        }
+    }
+    return GAMER_OK;
+}
+
+int fixup_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, int l, double dt) {
+    const gamer_level_t* L = H->levels;
+    const LevelCache& c = h->lv[l];
+    if (c.fix_list.empty()) return GAMER_OK;
+    const void* fc = L[l].face_flux ? L[l].face_flux : h->lv[l].own_flux;
+    const void* ff = L[l + 1].face_flux ? L[l + 1].face_flux : h->lv[l + 1].own_flux;
+    if (h->precision == GAMER_FP32) {
+        FixArgs<float> a{c.d_fix_list, (float*)L[l].u_out, (const float*)L[l + 1].u_out, L[l].nbr,
+                         L[l].child, (const float*)fc, (const float*)ff, L[l].n_groups,
+                         L[l + 1].n_groups, (float)(dt / L[l].dh)};
+        CK(h, launch_fixup<float>(a, (int)c.fix_list.size(), h->stream));
+    } else {
+        FixArgs<double> a{c.d_fix_list, (double*)L[l].u_out, (const double*)L[l + 1].u_out, L[l].nbr,
+                          L[l].child, (const double*)fc, (const double*)ff, L[l].n_groups,
+                          L[l + 1].n_groups, dt / L[l].dh};
+        CK(h, launch_fixup<double>(a, (int)c.fix_list.size(), h->stream));
+    }
+    return GAMER_OK;
+}
+
+template <typename T>
+int diag_launch(gamer_hydro_t h, const gamer_hierarchy_t* H) {
+    DiagArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    int item = 0;
+    for (int l = 0; l < H->n_levels; ++l) {
+        a.lv[l].u = static_cast<const T*>(H->levels[l].u);
+        a.lv[l].child = (l + 1 < H->n_levels) ? H->levels[l].child : nullptr;
+        a.lv[l].n_groups = H->levels[l].n_groups;
+        a.lv[l].item0 = item;
+        item += H->levels[l].n_groups;
+    }
+    a.n_levels = H->n_levels;
+    a.gamma = (T)h->gamma;
+    a.gm1 = (T)(h->gamma - 1.0);
+    a.pg_max = h->d_pg_max;
+    a.pg_sum = h->d_pg_sum;
+    a.pg_bad = h->d_pg_bad;
+    a.out = h->d_out;
+    CK(h, launch_diag<T>(a, item, h->stream));
+    return GAMER_OK;
+}
+
+int diagnose_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, double cfl, double* dt_out,
+                  double* sums, int64_t* n_bad) {
+    int r = prepare(h, H);
+    if (r) return r;
+    for (int l = 0; l < H->n_levels; ++l)
+        if (H->levels[l].n_groups > 0 && !H->levels[l].u) return fail(h, GAMER_ERR_ARG, "u is NULL");
+    r = h->precision == GAMER_FP32 ? diag_launch<float>(h, H) : diag_launch<double>(h, H);
+    if (r) return r;
+    CK(h, cudaMemcpyAsync(h->h_out, h->d_out, sizeof(DiagOut) * H->n_levels, cudaMemcpyDeviceToHost,
+                          h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (dt_out) {
+        double dt = INFINITY;
+        for (int l = 0; l < H->n_levels; ++l) {
+            if (H->levels[l].n_groups == 0) continue;
+            unsigned long long b = h->h_out[l].smax_bits;
+            double s;
+            memcpy(&s, &b, sizeof(s));
+            double d = H->levels[l].dh / s;
+            if (d < dt || d != d) dt = d;
+        }
+        *dt_out = cfl * dt;
+    }
+    if (sums) {
+        for (int v = 0; v < NV; ++v) sums[v] = 0.0;
+        for (int l = 0; l < H->n_levels; ++l) {
+            const double dh = H->levels[l].dh, dV = dh * dh * dh;
+            for (int v = 0; v < NV; ++v) sums[v] += h->h_out[l].sum[v] * dV;
+        }
+    }
+    if (n_bad) {
+        long long nb = 0;
+        for (int l = 0; l < H->n_levels; ++l) nb += h->h_out[l].n_bad;
+        *n_bad = nb;
+    }
+    return GAMER_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+
+extern "C" {
+
+int gamer_hydro_create(double gamma, int limiter, int ghost_width, int precision, gamer_hydro_t* out) {
+    if (!out) return fail(nullptr, GAMER_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!(gamma > 1.0) || !std::isfinite(gamma)) return fail(nullptr, GAMER_ERR_ARG, "gamma must be > 1");
+    if (limiter != GAMER_LIMITER_VANLEER && limiter != GAMER_LIMITER_MINMOD)
+        return fail(nullptr, GAMER_ERR_ARG, "unknown limiter");
+    if (precision != GAMER_FP32 && precision != GAMER_FP64)
+        return fail(nullptr, GAMER_ERR_ARG, "unknown precision");
+    if (ghost_width != NG)
+        return fail(nullptr, GAMER_ERR_UNSUPPORTED, "ghost_width must be 3 (seven-point stencil)");
+    gamer_hydro_t h = new gamer_hydro_s();
+    h->gamma = gamma;
+    h->limiter = limiter;
+    h->precision = precision;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_queue, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_dt, sizeof(double));
+    if (e != cudaSuccess) {
+        std::string m = std::string("CUDA initialisation failed: ") + cudaGetErrorString(e);
+        cudaFree(h->d_queue);
+        cudaFree(h->d_dt);
+        delete h;
+        return fail(nullptr, GAMER_ERR_CUDA, m);
+    }
+    *out = h;
+    return GAMER_OK;
+}
+
+int gamer_hydro_destroy(gamer_hydro_t h) {
+    if (!h) return GAMER_OK;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    drop_hierarchy(h);
+    cudaFree(h->d_queue);
+    cudaFree(h->d_dt);
+    cudaFree(h->d_pg_max);
+    cudaFree(h->d_pg_sum);
+    cudaFree(h->d_pg_bad);
+    cudaFree(h->d_out);
+    cudaFreeHost(h->h_out);
+    cudaFree(h->d_stage);
+    delete h;
+    return GAMER_OK;
+}
+
+int gamer_hydro_set_stream(gamer_hydro_t h, void* s) {
+    if (!h) return GAMER_ERR_ARG;
+    h->stream = static_cast<cudaStream_t>(s);
+    drop_graphs(h);
+    return GAMER_OK;
+}
+
+int gamer_hydro_set_parity(gamer_hydro_t h, int level, int parity) {
+    if (!h) return GAMER_ERR_ARG;
+    if (level < 0 || level >= 32 || (parity != 0 && parity != 1))
+        return fail(h, GAMER_ERR_ARG, "level must be in [0,32) and parity 0 or 1");
+    h->parity[level] = parity;
+    return GAMER_OK;
+}
+
+int gamer_hydro_get_parity(gamer_hydro_t h, int level, int* parity) {
+    if (!h || !parity) return GAMER_ERR_ARG;
+    if (level < 0 || level >= 32) return fail(h, GAMER_ERR_ARG, "level must be in [0,32)");
+    *parity = h->parity[level];
+    return GAMER_OK;
+}
+
+int gamer_hydro_cfl_dt(gamer_hydro_t h, const gamer_hierarchy_t* H, double cfl, double* dt_out) {
+    if (!h) return GAMER_ERR_ARG;
+    if (!dt_out) return fail(h, GAMER_ERR_ARG, "dt_out is NULL");
+    if (!(cfl > 0.0)) return fail(h, GAMER_ERR_ARG, "cfl must be positive");
+    CK(h, cudaSetDevice(h->device));
+    return diagnose_impl(h, H, cfl, dt_out, nullptr, nullptr);
+}
+
+int gamer_hydro_check(gamer_hydro_t h, const gamer_hierarchy_t* H, double sums[5], int64_t* n_bad) {
+    if (!h) return GAMER_ERR_ARG;
+    if (!sums || !n_bad) return fail(h, GAMER_ERR_ARG, "sums and n_bad are required");
+    CK(h, cudaSetDevice(h->device));
+    return diagnose_impl(h, H, 1.0, nullptr, sums, n_bad);
+}
+
+int gamer_hydro_diagnose(gamer_hydro_t h, const gamer_hierarchy_t* H, double cfl, double* dt_out,
+                         double sums[5], int64_t* n_bad) {
+    if (!h) return GAMER_ERR_ARG;
+    if (dt_out && !(cfl > 0.0)) return fail(h, GAMER_ERR_ARG, "cfl must be positive");
+    CK(h, cudaSetDevice(h->device));
+    return diagnose_impl(h, H, cfl, dt_out, sums, n_bad);
+}
+
+int gamer_hydro_advance(gamer_hydro_t h, const gamer_hierarchy_t* H, int level, double dt) {
+    if (!h) return GAMER_ERR_ARG;
+    if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(h, GAMER_ERR_ARG, "dt must be finite and >= 0");
+    CK(h, cudaSetDevice(h->device));
+    int r = prepare(h, H);
+    if (r) return r;
+    if ((r = check_level_arg(h, H, level))) return r;
+    r = advance_level_impl(h, H, level, dt, h->parity[level]);
+    if (r) return r;
+    h->parity[level] ^= 1;
+    return GAMER_OK;
+}
+
+int gamer_hydro_fixup(gamer_hydro_t h, const gamer_hierarchy_t* H, int level, double dt) {
+    if (!h) return GAMER_ERR_ARG;
+    if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(h, GAMER_ERR_ARG, "dt must be finite and >= 0");
+    CK(h, cudaSetDevice(h->device));
+    int r = prepare(h, H);
+    if (r) return r;
+    if (level < 0 || level + 1 >= H->n_levels)
+        return fail(h, GAMER_ERR_ARG, "fixup level must be in [0, n_levels-2]");
+    return fixup_impl(h, H, level, dt);
+}
+
+int gamer_hydro_advance_all(gamer_hydro_t h, const gamer_hierarchy_t* H, double dt) {
+    if (!h) return GAMER_ERR_ARG;
+    if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(h, GAMER_ERR_ARG, "dt must be finite and >= 0");
+    CK(h, cudaSetDevice(h->device));
+    int r = prepare(h, H);
+    if (r) return r;
+    const int n = H->n_levels;
+    const int order = h->parity[0];
+    for (int l = 1; l < n; ++l)
+        if (h->parity[l] != order)
+            return fail(h, GAMER_ERR_STATE, "advance_all needs every level at the same sweep parity");
+    if (h->precision == GAMER_FP32) {
+        SweepArgs<float> a;
+        memset(&a, 0, sizeof(a));
+        int item = 0;
+        for (int l = 0; l < n; ++l) {
+            fill_level<float>(a.lv[l], H->levels, l, h, dt);
+            a.lv[l].item0 = item;
+            item += H->levels[l].n_groups;
+        }
+        a.n_levels = n;
+        a.total = item;
+        a.queue = h->d_queue;
+        a.gamma = (float)h->gamma;
+        a.gm1 = (float)(h->gamma - 1.0);
+        if (item > 0) {
+            CK(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), h->stream));
+            const int grid = std::min(item, h->sm_count);
+            CK(h, launch_sweep_f32(a, order, h->limiter, h->sweep_threads, grid, h->stream));
+        }
+    } else {
+        for (int l = 0; l < n; ++l)
+            if ((r = advance_level_impl(h, H, l, dt, order))) return r;
+    }
+    for (int l = n - 2; l >= 0; --l)
+        if ((r = fixup_impl(h, H, l, dt))) return r;
+    for (int l = 0; l < n; ++l) h->parity[l] ^= 1;
+    return GAMER_OK;
+}
+
+const char* gamer_hydro_last_error(gamer_hydro_t h) {
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+}  // extern "C"

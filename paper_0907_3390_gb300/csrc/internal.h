@@ -1,0 +1,62 @@
+// internal.h -- declarations shared between the kernel files and the C-ABI
+// host code (not part of the public interface).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace gh {
+
+// ---- sweep kernels
+cudaError_t launch_sweep_f32(const SweepArgs<float>& a, int order, int lim, int threads, int grid,
+                             cudaStream_t st);
+size_t sweep_f32_smem();
+cudaError_t launch_pg_f64(const LevelArgs<double>& L, int g0, int count, int order, int lim,
+                          double gamma, double gm1, double* stage, cudaStream_t st);
+size_t stage_f64_bytes_per_group();
+
+// ---- fix-up: coarse level c corrected from fine level c+1
+template <typename T>
+struct FixArgs {
+    const int* list;      // coarse patches to visit
+    T* uc;                // coarse u_out
+    const T* uf;          // fine u_out
+    const int* nbr;       // coarse map
+    const int* child;     // coarse child map
+    const T* flux_c;      // coarse face fluxes
+    const T* flux_f;      // fine face fluxes
+    int n_c, n_f;         // groups on the two levels
+    T lam;                // dt / dh of the coarse level
+};
+template <typename T>
+cudaError_t launch_fixup(const FixArgs<T>& a, int n_list, cudaStream_t st);
+
+// ---- diagnostics
+template <typename T>
+struct DiagLevel {
+    const T* u;
+    const int* child;
+    int n_groups;
+    int item0;
+};
+struct DiagOut {
+    unsigned long long smax_bits;  // bit pattern of the largest signal speed
+    double sum[NV];                // leaf sums of u (not yet times dV)
+    long long n_bad;
+};
+template <typename T>
+struct DiagArgs {
+    DiagLevel<T> lv[MAXLEV];
+    int n_levels;
+    T gamma, gm1;
+    unsigned long long* pg_max;   // [total]
+    double* pg_sum;               // [total][5]
+    int* pg_bad;                  // [total]
+    DiagOut* out;                 // [n_levels]
+};
+template <typename T>
+cudaError_t launch_diag(const DiagArgs<T>& a, int total, cudaStream_t st);
+
+}  // namespace gh

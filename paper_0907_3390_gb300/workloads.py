@@ -67,7 +67,7 @@ def grf(n: int, rng: np.random.Generator, index: float = -2.0) -> np.ndarray:
     amp = np.zeros_like(k)
     nz = k > 0
     amp[nz] = k[nz] ** (index / 2.0)
-    d = np.fft.irfftn(f * amp, s=(n, n, n))
+    d = np.fft.irfftn(f * amp, s=(n, n, n), axes=(0, 1, 2))
     d -= d.mean()
     d /= d.std()
     return d
@@ -207,7 +207,7 @@ def smoothed(field: np.ndarray, R: float) -> np.ndarray:
     n = field.shape[0]
     k2 = (np.fft.rfftfreq(n)[None, None, :] ** 2 + np.fft.fftfreq(n)[None, :, None] ** 2 +
           np.fft.fftfreq(n)[:, None, None] ** 2) * (2 * np.pi) ** 2
-    return np.fft.irfftn(np.fft.rfftn(field) * np.exp(-0.5 * k2 * R * R), s=field.shape)
+    return np.fft.irfftn(np.fft.rfftn(field) * np.exp(-0.5 * k2 * R * R), s=field.shape, axes=(0, 1, 2))
 
 
 def amr_grf(seed: int = 1002, base_n: int = 128, targets=(4096, 9000, 21000), n_field: int = 128,

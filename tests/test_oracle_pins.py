@@ -361,8 +361,9 @@ def test_coarse_ghosts_exact_on_linear_data():
 
 def test_amr_uniform_flow_bitwise():
     H = two_level(2, box=[(1, 3), (0, 2), (1, 3)])
-    u = lambda x, y, z, dh: (np.full(x.shape, 1.3), np.full(x.shape, 0.4), np.full(x.shape, -0.7),
-                             np.full(x.shape, 0.25), np.full(x.shape, 0.9))
+    # dyadic values: the 8-child sums of the restriction are exact
+    u = lambda x, y, z, dh: (np.full(x.shape, 1.25), np.full(x.shape, 0.5), np.full(x.shape, -0.75),
+                             np.full(x.shape, 0.25), np.full(x.shape, 0.875))
     states = wl.level_fields(H, u)
     O = oracle.OracleLevels(H, states)
     oracle.run(O, G, 0.5, 4)
