@@ -1,0 +1,428 @@
+#!/usr/bin/env python3
+"""Benchmark of the relaxing-TVD patch-group hydro path on GB300.
+
+A step is one pass of the whole hot path over the workload: one sweep set
+of every patch group (ghost gather + x/y/z or z/y/x sweeps, fused in one
+persistent FP32 launch), then the diagnostics (CFL time step and the
+conservation / positivity check, FP64 reductions) whose dt feeds the next
+step.  The default workload is the periodic 128^3 smooth k^-2 random field
+(4096 patches of 8^3 = 512 patch groups).  It fits in L2, so L2 is flushed
+(a 256 MiB write) before every timed step, outside the timed interval.
+
+Prints ONE JSON line (rank 0).  See --help for options.  ``--impl
+reference`` times the FP64 CPU oracle instead (on a bounded sample of the
+same workload per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s and % of HBM roofline, FP32 batched vs plain FP64, at stated L1 err"
+UNIT = "cell-updates/s"
+GAMMA = 5.0 / 3.0
+CFL = 0.5
+BYTES_PER_CELL_F32 = (22 ** 3 + 16 ** 3) * 5 * 4 / 16 ** 3   # 72.0: padded read + interior write
+BYTES_PER_CELL_F64 = 2 * BYTES_PER_CELL_F32
+
+
+def parse():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="uniform128", choices=sorted(WORKLOADS))
+    p.add_argument("--quick", action="store_true",
+                   help="device-timed value only (no e2e, FP64, L1, CPU baseline, clocks); for profiling")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------ workloads
+
+def _wl_uniform(n, kind):
+    def make():
+        from paper_0907_3390_gb300 import workloads as W
+        if kind == "smooth":
+            u, npg = W.smooth_grf(n, seed=1001)
+        else:
+            u, npg = W.lognormal_grf(n, seed=1003)
+        H, st = W.single_level(u, npg)
+        return H, st
+    return make
+
+
+def _wl_amr(kind):
+    def make():
+        from paper_0907_3390_gb300 import workloads as W
+        if kind == "amr3":
+            return W.amr_grf()
+        return W.amr_stress("lognormal")
+    return make
+
+
+WORKLOADS = {
+    "uniform128": ("smooth k^-2 Gaussian random fields (density contrast 10, rms Mach 1), periodic "
+                   "128^3, 4096 patches of 8^3 (512 patch groups), gamma 5/3, CFL 0.5", _wl_uniform(128, "smooth")),
+    "uniform256": ("smooth k^-2 Gaussian random fields, periodic 256^3, 32768 patches", _wl_uniform(256, "smooth")),
+    "uniform512": ("lognormal k^-2 density (sigma 1.5), rms Mach 3, periodic 512^3, 262144 patches",
+                   _wl_uniform(512, "lognormal")),
+    "amr3": ("3 levels over a 128^3 base, 4096/9000/21000 patches, lognormal k^-2 density", _wl_amr("amr3")),
+    "amr4": ("4 levels, 32768 patches, lognormal sigma 2.5 density, converging flows up to Mach 20",
+             _wl_amr("amr4")),
+}
+
+
+# ------------------------------------------------------------ helpers
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("sweep_f32.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_0907_3390_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_cell():
+    """DRAM bytes per cell-update of the FP32 sweep kernel from the committed
+    ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "sweep_f32_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("source_sha") != kernel_source_sha():
+        return None
+    return float(d["dram_bytes_per_cell"])
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.remove(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_rate(H, states, seconds, threads):
+    """Oracle (plain FP64 C, OpenMP over patch groups) on a bounded sample of
+    the workload's patch groups: cell-updates/s and the sample description."""
+    import oracle
+    oracle.set_threads(threads)
+    O = oracle.OracleLevels(H, [np.asarray(s, dtype=np.float64) for s in states])
+    dt = O.cfl_dt(GAMMA, CFL)
+    lv = 0
+    n = H.levels[lv].n_groups
+    probe = min(n, max(threads, 8))
+    t0 = time.perf_counter()
+    O.advance_level(lv, GAMMA, dt, 0, groups=np.arange(probe))
+    t1 = time.perf_counter() - t0
+    count = int(min(n, max(probe, probe * seconds / max(t1, 1e-6))))
+    groups = np.arange(count)
+    t0 = time.perf_counter()
+    O.advance_level(lv, GAMMA, dt, 0, groups=groups)
+    el = time.perf_counter() - t0
+    return count * 4096 / el, f"{count} of {n} patch groups of level {lv}, one xyz sweep set", el
+
+
+# ------------------------------------------------------------ reference arm
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    desc, make = WORKLOADS[args.workload]
+    H, st = make()
+    import oracle
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    O = oracle.OracleLevels(H, st)
+    dt = O.cfl_dt(GAMMA, CFL)
+    n = H.levels[0].n_groups
+    # each step: a bounded sample of the workload (whole groups), sized so the
+    # whole --steps/--warmup run ends within a few minutes
+    probe = min(n, max(threads, 8))
+    t0 = time.perf_counter()
+    O.advance_level(0, GAMMA, dt, 0, groups=np.arange(probe))
+    t1 = time.perf_counter() - t0
+    per_step_s = max(1.0, 150.0 / max(args.steps + args.warmup, 1))
+    count = int(min(n, max(probe, probe * per_step_s / max(t1, 1e-6))))
+    groups = np.arange(count)
+    for w in range(args.warmup):
+        O.advance_level(0, GAMMA, dt, w % 2, groups=groups)
+    el = 0.0
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        O.advance_level(0, GAMMA, dt, s % 2, groups=groups)
+        el += time.perf_counter() - t0
+    rate = count * 4096 * args.steps / el
+    sample = f"{count} of {n} patch groups per step (one sweep set each)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": desc, "sample": sample},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------ our arm
+
+def run_ours(args, rank, world, dist):
+    import torch
+    from paper_0907_3390_gb300 import binding as B
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    desc, make = WORKLOADS[args.workload]
+    H, st = make()
+    cells = sum(lv.n_groups for lv in H.levels) * 4096
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    S = B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP32, stream=stream)
+    D = B.DeviceHierarchy(H, st, torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    dt = B.gamer_hydro_cfl_dt(S.h, D, CFL)
+    state = {"dt": dt}
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        B.gamer_hydro_advance_all(S.h, D, state["dt"])
+        if ev is not None:
+            ev[1].record(stream)
+        D.swap()
+        dtn, sums, nb = B.gamer_hydro_diagnose(S.h, D, CFL)
+        if B.gamer_hydro_get_parity(S.h, 0) == 0:   # next call is xyz: new dt (held for zyx)
+            state["dt"] = dtn
+        return sums, nb
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sums0, _ = step()
+
+    clocks = None if args.quick else ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    n_bad = 0
+    for s in range(args.steps):
+        flush.fill_(float(s))                       # evict L2 (outside the timed interval)
+        ev[s][0].record(stream)
+        sums, nb = step(kev[s])
+        ev[s][1].record(stream)
+        n_bad += nb
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop() if clocks else None
+    step_ms = sum(a.elapsed_time(b) for a, b in ev)
+    kern_ms = [a.elapsed_time(b) for a, b in kev]
+    t_local = step_ms / 1e3
+    if dist is not None:
+        t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    value = cells * args.steps * world / t_max
+    res = {"value": value, "ms_per_step": 1e3 * t_max / args.steps}
+
+    hbm, peak_kind = measured_peaks()
+    k_avg = float(np.mean(kern_ms)) / 1e3
+    achieved = BYTES_PER_CELL_F32 * cells / k_avg / 1e9
+    tpc = traffic_per_cell()
+    res["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                       "frac": achieved / hbm, "peak_kind": f"{peak_kind} copy bandwidth",
+                       "traffic": None if tpc is None else tpc * cells,
+                       "kernel": "k_sweep_f32 (gather + 3 sweeps + store, one persistent launch)",
+                       "kernel_ms": 1e3 * k_avg, "algorithmic_bytes": BYTES_PER_CELL_F32 * cells}
+    res["clocks"] = clk
+    conservation = None
+    if not args.quick:
+        conservation = float(np.max(np.abs(sums - sums0) / (np.abs(sums0) + 1e-30)))
+
+    extras = {}
+    if not args.quick and rank == 0:
+        extras = run_extras(args, B, torch, H, st, cells, dev, stream)
+    S.close()
+    return res, extras, cells, n_bad, conservation, desc
+
+
+def run_extras(args, B, torch, H, st, cells, dev, stream):
+    out = {}
+    # ---- e2e through the C ABI with host buffers: H2D of the state, the
+    # step, D2H of the new state, every step
+    S = B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP32, stream=stream)
+    D = B.DeviceHierarchy(H, st, torch.float32, device=dev)
+    host_in = [x.cpu().pin_memory() for x in D.u]
+    host_out = [torch.empty_like(x) for x in host_in]
+    dt = B.gamer_hydro_cfl_dt(S.h, D, CFL)
+    n_e2e = max(3, min(args.steps, 10))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for it in range(2 + n_e2e):
+        if it == 2:
+            torch.cuda.synchronize()
+            e0.record(stream)
+        for l in range(len(D.u)):
+            D.u[l].copy_(host_in[l], non_blocking=True)
+        B.gamer_hydro_advance_all(S.h, D, dt)
+        D.swap()
+        dtn, sums, nb = B.gamer_hydro_diagnose(S.h, D, CFL)
+        for l in range(len(D.u)):
+            host_out[l].copy_(D.u[l], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n_e2e
+    nbytes = sum(x.numel() * 4 for x in host_in)
+    out["e2e"] = {"value": cells / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                  "d2h_bytes_per_step": nbytes + 8 * 7}
+    S.close()
+
+    # ---- plain FP64 GPU path (one block per patch group) and the per-field
+    # L1 error of one FP32 sweep set against it (the FP64 path is
+    # bit-identical to the FP64 oracle in the parity tests)
+    S64 = B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP64, stream=stream)
+    D64 = B.DeviceHierarchy(H, st, torch.float64, device=dev)
+    dt = B.gamer_hydro_cfl_dt(S64.h, D64, CFL)
+    S32 = B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP32, stream=stream)
+    D32 = B.DeviceHierarchy(H, st, torch.float32, device=dev)
+    S32.step(D32, dt)
+    S64.step(D64, dt)
+    ref = D64.u[0].double()
+    got = D32.u[0].double()
+    scale = ref.reshape(5, -1).abs().max(dim=1).values
+    l1 = ((got - ref).reshape(5, -1).abs().mean(dim=1) / scale).cpu().numpy()
+    n64 = 3
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(n64):
+        B.gamer_hydro_advance_all(S64.h, D64, dt)
+        D64.swap()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1) / n64
+    out["fp64_plain"] = {"value": cells / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                         "note": "advance only, one thread block per patch group, FP64 throughout"}
+    out["l1_rel_err_fp32_vs_fp64"] = {"fields": ["rho", "mx", "my", "mz", "e"], "value": [float(x) for x in l1],
+                                      "after": "one sweep set"}
+    S64.close()
+    S32.close()
+
+    # ---- the oracle on the host cores, bounded sample
+    threads = os.cpu_count() or 1
+    rate, sample, secs = cpu_oracle_rate(H, st, args.cpu_seconds, threads)
+    out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                           "seconds": secs}
+    return out
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist_mod.init_process_group(backend=backend)
+        dist = dist_mod
+    if args.impl == "reference":
+        rc = run_reference(args, rank, world)
+        if dist is not None:
+            dist.destroy_process_group()
+        return rc
+    res, extras, cells, n_bad, cons, desc = run_ours(args, rank, world, dist)
+    if rank == 0:
+        steps = args.steps
+        line = {
+            "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "cells_per_gpu": cells, "precision": "FP32 batched, FP64 reductions",
+                       "step": "advance_all (gather + 3 sweeps) + diagnose (CFL dt, sums, positivity)",
+                       "l2": "flushed before every timed step (256 MiB write, outside the timed interval)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "roofline": res["roofline"],
+            "gpu_launches": 3 * steps,
+            "clocks": res["clocks"],
+            "n_bad_cells": n_bad,
+        }
+        if cons is not None:
+            line["conservation_drift_rel"] = cons
+        for k in ("e2e", "cpu_baseline", "fp64_plain", "l1_rel_err_fp32_vs_fp64"):
+            if k in extras:
+                line[k] = extras[k]
+        if "fp64_plain" in extras:
+            line["fp32_over_fp64_plain"] = res["value"] / extras["fp64_plain"]["value"]
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -18,7 +18,8 @@
  * - Conserved state of a level: u[5][8*n_groups][8][8][8], variables
  *   (rho, rho vx, rho vy, rho vz, e), x fastest; patch group g owns patches
  *   8g..8g+7, local patch index (pz*2 + py)*2 + px.  Element type float for
- *   GAMER_FP32 handles, double for GAMER_FP64 handles.
+ *   GAMER_FP32 handles, double for GAMER_FP64 handles.  u and u_out must be
+ *   16-byte aligned (GAMER_ERR_ARG otherwise).
  * - nbr[n_groups][26]: neighbour d = (dz+1)*9 + (dy+1)*3 + (dx+1) with 13
  *   (the group itself) skipped: a same-level group index >= 0, -1 when that
  *   region exists only on the coarser level (ghosts interpolated), -2 for

@@ -9,7 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/gamer_hydro.h"
+#include "gamer_hydro.h"
 #include "internal.h"
 
 using namespace gh;
@@ -301,6 +301,21 @@ int prepare(gamer_hydro_t h, const gamer_hierarchy_t* H) {
     return ensure_diag(h, total);
 }
 
+// Per-call pointer checks (u / u_out may change on every call).
+int check_pointers(gamer_hydro_t h, const gamer_hierarchy_t* H, bool need_out) {
+    for (int l = 0; l < H->n_levels; ++l) {
+        const gamer_level_t& L = H->levels[l];
+        if (L.n_groups == 0) continue;
+        if (!L.u || !L.nbr) return fail(h, GAMER_ERR_ARG, "u and nbr are required on level " + std::to_string(l));
+        if (need_out && !L.u_out) return fail(h, GAMER_ERR_ARG, "u_out is NULL on level " + std::to_string(l));
+        if (need_out && L.u == L.u_out) return fail(h, GAMER_ERR_ARG, "u_out must not alias u");
+        // the FP32 kernels move 16-byte quads of patch rows
+        if ((reinterpret_cast<uintptr_t>(L.u) | (need_out ? reinterpret_cast<uintptr_t>(L.u_out) : 0)) & 15)
+            return fail(h, GAMER_ERR_ARG, "u and u_out must be 16-byte aligned");
+    }
+    return GAMER_OK;
+}
+
 int check_level_arg(gamer_hydro_t h, const gamer_hierarchy_t* H, int level) {
     if (level < 0 || level >= H->n_levels) return fail(h, GAMER_ERR_ARG, "level out of range");
     return GAMER_OK;
@@ -388,8 +403,7 @@ int diagnose_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, double cfl, doubl
                   double* sums, int64_t* n_bad) {
     int r = prepare(h, H);
     if (r) return r;
-    for (int l = 0; l < H->n_levels; ++l)
-        if (H->levels[l].n_groups > 0 && !H->levels[l].u) return fail(h, GAMER_ERR_ARG, "u is NULL");
+    if ((r = check_pointers(h, H, false))) return r;
     r = h->precision == GAMER_FP32 ? diag_launch<float>(h, H) : diag_launch<double>(h, H);
     if (r) return r;
     CK(h, cudaMemcpyAsync(h->h_out, h->d_out, sizeof(DiagOut) * H->n_levels, cudaMemcpyDeviceToHost,
@@ -527,6 +541,7 @@ int gamer_hydro_advance(gamer_hydro_t h, const gamer_hierarchy_t* H, int level, 
     int r = prepare(h, H);
     if (r) return r;
     if ((r = check_level_arg(h, H, level))) return r;
+    if ((r = check_pointers(h, H, true))) return r;
     r = advance_level_impl(h, H, level, dt, h->parity[level]);
     if (r) return r;
     h->parity[level] ^= 1;
@@ -539,6 +554,7 @@ int gamer_hydro_fixup(gamer_hydro_t h, const gamer_hierarchy_t* H, int level, do
     CK(h, cudaSetDevice(h->device));
     int r = prepare(h, H);
     if (r) return r;
+    if ((r = check_pointers(h, H, true))) return r;
     if (level < 0 || level + 1 >= H->n_levels)
         return fail(h, GAMER_ERR_ARG, "fixup level must be in [0, n_levels-2]");
     return fixup_impl(h, H, level, dt);
@@ -550,6 +566,7 @@ int gamer_hydro_advance_all(gamer_hydro_t h, const gamer_hierarchy_t* H, double 
     CK(h, cudaSetDevice(h->device));
     int r = prepare(h, H);
     if (r) return r;
+    if ((r = check_pointers(h, H, true))) return r;
     const int n = H->n_levels;
     const int order = h->parity[0];
     for (int l = 1; l < n; ++l)

@@ -36,9 +36,12 @@ namespace gh {
 
 constexpr int XP = 23;                    // x pitch: odd, so x-sweep columns hit distinct banks
 constexpr int VS = PD * PD * XP;          // floats per variable in shared memory
-constexpr size_t SMEM_F32 = (size_t)NV * VS * sizeof(float) + 256 * sizeof(int);
+constexpr size_t SMEM_F32 = (size_t)NV * VS * sizeof(float) + 256 * sizeof(int);   // block + 2 item tables
 
-// A = c u + F and B = c u - F of one cell, sweep along AXIS.
+// A = c u + F (= 2 F^R) and B = c u - F (= 2 F^L) of one cell for a sweep
+// along AXIS (Eq. LRFlux with w = F/c substituted): c = |v_n| + c_s
+// (Sec. 2.2), F = (m_n, m v_n + P e_n, (e + P) v_n), P from Eqs.
+// ThermalEnergy, EOS.
 template <int AXIS>
 __device__ __forceinline__ void state(const float u[NV], float g, float gm1, float A[NV], float B[NV]) {
     const float r = u[0];
@@ -63,6 +66,9 @@ __device__ __forceinline__ void state(const float u[NV], float g, float gm1, flo
     }
 }
 
+// psi(x, y) = 2 phi(x/4, y/4): by homogeneity of the limiter, on unhalved
+// differences of A or B.  van Leer (Eq. vanLeer): xy/(x+y) when xy > 0;
+// minmod: min(|x|,|y|)/2 with the common sign; zero otherwise.
 template <int LIM>
 __device__ __forceinline__ float psi(float x, float y) {
     const float p = x * y;
@@ -75,98 +81,119 @@ __device__ __forceinline__ float psi(float x, float y) {
     }
 }
 
-// One 1-D column of 22 cells starting at p (stride S between cells, VS
-// between variables) along AXIS; cells 3..18 are overwritten with the
-// full-step values.  fl: face-flux slot of this row ([3 planes][5][256]
-// with plane stride 5*256), or nullptr.
-template <int AXIS, int S, int LIM>
-__device__ __forceinline__ void column(float* __restrict__ p, float lam4, float lam2, float g,
-                                       float gm1, float* __restrict__ fl) {
-    float u1[NV], u2[NV], u3[NV];          // u_{k-1}, u_{k-2}, u_{k-3}
-    float Ap[NV];                          // A_{k-1}
-    float Hp[NV];                          // half-step flux at k-3/2 (x2)
-    float Aq[NV], Bq[NV];                  // A', B' of the midpoint state at k-2
-    float dAp[NV], dBp[NV];                // dA', dB' at k-5/2
-    float Ahp[NV];                         // A'_{n+1/2} at k-5/2
-    float Gp[NV];                          // net flux (x2) at k-7/2
+// Register state carried along one column.
+struct ColState {
+    float u1[NV];          // u_{k-1}
+    float Ap[NV];          // A_{k-1}
+    float Hp[NV];          // half-step flux (x2) at interface k-3/2
+    float Aq[NV], Bq[NV];  // A', B' of the midpoint state of cell k-2
+    float dAp[NV], dBp[NV];// dA', dB' at interface k-5/2
+    float Ahp[NV];         // TVD A' flux at interface k-5/2
+    float Gp[NV];          // net flux (x2) at interface k-7/2
+};
+
+// Step k of the stream along a column.  K = min(k, 6) is the fill level of
+// the pipeline (compile time): cell k enters (K >= 0); the half-step flux
+// at k-1/2 forms (K >= 1, Eq. MidpointValue with first-order upwind
+// fluxes); the midpoint state of cell k-1 and its A', B' form (K >= 2);
+// the differences at k-3/2 (K >= 3); the TVD fluxes A'_{k-3/2} and
+// B'_{k-5/2} (K >= 4, Eqs. 2ndTVDFluxCorr..2ndRFlux and their left-moving
+// mirror); the net flux at k-5/2 (K >= 5); the full step of cell k-3
+// (K >= 6, Eq. FullstepValue).
+template <int AXIS, int S, int LIM, int K>
+__device__ __forceinline__ void col_step(float* __restrict__ p, int k, ColState& c, float lam4,
+                                         float lam2, float g, float gm1, float* __restrict__ fl) {
+    float u[NV], A[NV], B[NV];
 #pragma unroll
-    for (int k = 0; k < PD; ++k) {
-        float u[NV], A[NV], B[NV];
+    for (int v = 0; v < NV; ++v) u[v] = p[k * S + v * VS];
+    state<AXIS>(u, g, gm1, A, B);
+    if (K >= 1) {
+        float H[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) u[v] = p[k * S + v * VS];
-        state<AXIS>(u, g, gm1, A, B);
-        if (k >= 1) {
-            float H[NV];
+        for (int v = 0; v < NV; ++v) H[v] = c.Ap[v] - B[v];
+        if (K >= 2) {
+            float uh[NV], A1[NV], B1[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) H[v] = Ap[v] - B[v];
-            if (k >= 2) {
-                float uh[NV], A1[NV], B1[NV];
+            for (int v = 0; v < NV; ++v) uh[v] = fmaf(-lam4, H[v] - c.Hp[v], c.u1[v]);
+            state<AXIS>(uh, g, gm1, A1, B1);
+            if (K >= 3) {
+                float dA[NV], dB[NV];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) uh[v] = fmaf(-lam4, H[v] - Hp[v], u1[v]);
-                state<AXIS>(uh, g, gm1, A1, B1);
-                if (k >= 3) {
-                    float dA[NV], dB[NV];
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) {
-                        dA[v] = A1[v] - Aq[v];
-                        dB[v] = B1[v] - Bq[v];
-                    }
-                    if (k >= 4) {
-                        float Ah[NV], Bh[NV];
-#pragma unroll
-                        for (int v = 0; v < NV; ++v) {
-                            Ah[v] = Aq[v] + psi<LIM>(dAp[v], dA[v]);
-                            Bh[v] = Bq[v] - psi<LIM>(dB[v], dBp[v]);
-                        }
-                        if (k >= 5) {
-                            float Gn[NV];
-#pragma unroll
-                            for (int v = 0; v < NV; ++v) Gn[v] = Ahp[v] - Bh[v];
-                            if ((k == 5 || k == 13 || k == 21) && fl != nullptr) {
-#pragma unroll
-                                for (int v = 0; v < NV; ++v)
-                                    fl[((k - 5) / 8) * (NV * 256) + v * 256] = 0.5f * Gn[v];
-                            }
-                            if (k >= 6) {
-#pragma unroll
-                                for (int v = 0; v < NV; ++v)
-                                    p[(k - 3) * S + v * VS] = fmaf(-lam2, Gn[v] - Gp[v], u3[v]);
-                            }
-#pragma unroll
-                            for (int v = 0; v < NV; ++v) Gp[v] = Gn[v];
-                        }
-#pragma unroll
-                        for (int v = 0; v < NV; ++v) Ahp[v] = Ah[v];
-                    }
+                for (int v = 0; v < NV; ++v) {
+                    dA[v] = A1[v] - c.Aq[v];
+                    dB[v] = B1[v] - c.Bq[v];
+                }
+                if (K >= 4) {
+                    float G[NV];
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
-                        dAp[v] = dA[v];
-                        dBp[v] = dB[v];
+                        const float Ah = c.Aq[v] + psi<LIM>(c.dAp[v], dA[v]);
+                        const float Bh = c.Bq[v] - psi<LIM>(dB[v], c.dBp[v]);
+                        G[v] = c.Ahp[v] - Bh;                    // net flux (x2) at k-5/2
+                        c.Ahp[v] = Ah;
+                    }
+                    if (K >= 5) {
+                        if (fl != nullptr && ((k - 5) & 7) == 0) {
+#pragma unroll
+                            for (int v = 0; v < NV; ++v) fl[((k - 5) >> 3) * (NV * 256) + v * 256] = 0.5f * G[v];
+                        }
+                        if (K >= 6) {
+#pragma unroll
+                            for (int v = 0; v < NV; ++v) {
+                                const float un = p[(k - 3) * S + v * VS];
+                                p[(k - 3) * S + v * VS] = fmaf(-lam2, G[v] - c.Gp[v], un);
+                            }
+                        }
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) c.Gp[v] = G[v];
                     }
                 }
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    Aq[v] = A1[v];
-                    Bq[v] = B1[v];
+                    c.dAp[v] = dA[v];
+                    c.dBp[v] = dB[v];
                 }
             }
 #pragma unroll
-            for (int v = 0; v < NV; ++v) Hp[v] = H[v];
+            for (int v = 0; v < NV; ++v) {
+                c.Aq[v] = A1[v];
+                c.Bq[v] = B1[v];
+            }
         }
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            Ap[v] = A[v];
-            u3[v] = u2[v];
-            u2[v] = u1[v];
-            u1[v] = u[v];
-        }
+        for (int v = 0; v < NV; ++v) c.Hp[v] = H[v];
     }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        c.Ap[v] = A[v];
+        c.u1[v] = u[v];
+    }
+}
+
+// One 1-D column of 22 cells starting at p (stride S between cells, VS
+// between variables) along AXIS; cells 3..18 are overwritten with the
+// full-step values.  fl: face-flux slot of this row ([3 planes][5][256]
+// with plane stride 5*256), or nullptr.  Cells 0..5 fill the pipeline
+// (unrolled), cells 6..21 run the rolled steady-state step, which keeps the
+// code small enough for the instruction cache.
+template <int AXIS, int S, int LIM>
+__device__ __forceinline__ void column(float* __restrict__ p, float lam4, float lam2, float g,
+                                       float gm1, float* __restrict__ fl) {
+    ColState c;
+    col_step<AXIS, S, LIM, 0>(p, 0, c, lam4, lam2, g, gm1, fl);
+    col_step<AXIS, S, LIM, 1>(p, 1, c, lam4, lam2, g, gm1, fl);
+    col_step<AXIS, S, LIM, 2>(p, 2, c, lam4, lam2, g, gm1, fl);
+    col_step<AXIS, S, LIM, 3>(p, 3, c, lam4, lam2, g, gm1, fl);
+    col_step<AXIS, S, LIM, 4>(p, 4, c, lam4, lam2, g, gm1, fl);
+    col_step<AXIS, S, LIM, 5>(p, 5, c, lam4, lam2, g, gm1, fl);
+#pragma unroll 2
+    for (int k = 6; k < PD; ++k) col_step<AXIS, S, LIM, 6>(p, k, c, lam4, lam2, g, gm1, fl);
 }
 
 // Sweep s (0,1,2) of order ORDER over the shared block; columns whose
 // transverse axes were swept earlier in this set only cover [3,19).
-template <int NT, int ORDER, int S_IDX, int LIM>
-__device__ __forceinline__ void sweep(float* sm, float lam, float g, float gm1, float* flux_g) {
+template <int ORDER, int S_IDX, int LIM>
+__device__ __forceinline__ void sweep(float* sm, float lam, float g, float gm1, float* flux_g, int nact) {
     constexpr int AX = ORDER == 0 ? S_IDX : 2 - S_IDX;
     constexpr int T1 = AX == 0 ? 1 : 0;
     constexpr int T2 = AX == 2 ? 1 : 2;
@@ -178,7 +205,8 @@ __device__ __forceinline__ void sweep(float* sm, float lam, float g, float gm1, 
     constexpr int ST[3] = {1, XP, PD * XP};
     constexpr int S = ST[AX];
     const float lam4 = 0.25f * lam, lam2 = 0.5f * lam;
-    for (int c = threadIdx.x; c < N1 * N2; c += NT) {
+    if ((int)threadIdx.x >= nact) return;
+    for (int c = threadIdx.x; c < N1 * N2; c += nact) {
         const int i1 = LO1 + c % N1, i2 = LO2 + c / N1;
         float* p = sm + i1 * ST[T1] + i2 * ST[T2];
         float* fl = nullptr;
@@ -188,87 +216,287 @@ __device__ __forceinline__ void sweep(float* sm, float lam, float g, float gm1, 
     }
 }
 
-template <int NT, int ORDER, int LIM>
-__global__ void __launch_bounds__(NT, 1) k_sweep_f32(const SweepArgs<float> args) {
-    extern __shared__ float sm[];
-    int* s_int = reinterpret_cast<int*>(sm + NV * VS);
-    int* s_src = s_int;          // [27]
-    int* s_mask = s_int + 32;    // [27]
-    int* s_csrc = s_int + 64;    // [27]
-    int* s_cmask = s_int + 96;   // [27]
-    int* s_par = s_int + 128;    // parent patch
-    int* s_item = s_int + 129;   // current work item
+// ---------------------------------------------------------------- gather
 
-    for (;;) {
-        if (threadIdx.x == 0) *s_item = atomicAdd(args.queue, 1);
-        __syncthreads();
-        const int item = *s_item;
-        if (item >= args.total) break;
-        int l = 0;
-        while (l + 1 < args.n_levels && item >= args.lv[l + 1].item0) ++l;
-        const LevelArgs<float>& L = args.lv[l];
-        const int g = item - L.item0;
+__device__ __forceinline__ float4 ldg4(const float* p) {
+    return __ldg(reinterpret_cast<const float4*>(p));
+}
 
-        build_tables<float>(L, g, s_src, s_mask, s_csrc, s_cmask, s_par);
-        __syncthreads();
-        int ppx = 0, ppy = 0, ppz = 0;
-        if (*s_par >= 0) {
-            const int lp = *s_par & 7;
-            ppx = lp & 1; ppy = (lp >> 1) & 1; ppz = (lp >> 2) & 1;
-        }
-        gather_block<float, XP, NT>(sm, VS, L, g, s_src, s_mask, s_csrc, s_cmask, ppx, ppy, ppz);
-        __syncthreads();
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
-        float* fg = L.flux ? L.flux + (size_t)g * FLUX_PG : nullptr;
-        sweep<NT, ORDER, 0, LIM>(sm, L.lam, args.gamma, args.gm1, fg);
-        __syncthreads();
-        sweep<NT, ORDER, 1, LIM>(sm, L.lam, args.gamma, args.gm1, fg);
-        __syncthreads();
-        sweep<NT, ORDER, 2, LIM>(sm, L.lam, args.gamma, args.gm1, fg);
-        __syncthreads();
+// Work-item context in shared memory: region tables of the group and of its
+// parent's coarse group, level, group index and parent patch.
+struct ItemTab {
+    int src[27], mask[27], csrc[27], cmask[27];
+    int item, level, g, par;
+};
 
-        // interior -> u_out, coalesced along patch rows
-        const size_t vstride = (size_t)L.n_groups * 8 * 512;
-        float* out = L.u_out + ((size_t)g << 12);
-        for (int i = threadIdx.x; i < CELLS_PG; i += NT) {
-            // i enumerates the group's 8 patches in storage order
-            const int patch = i >> 9, w = i & 511;
-            const int x = ((patch & 1) << 3) | (w & 7);
-            const int y = (((patch >> 1) & 1) << 3) | ((w >> 3) & 7);
-            const int z = ((patch >> 2) << 3) | (w >> 6);
-            const float* s = sm + ((z + NG) * PD + (y + NG)) * XP + (x + NG);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) out[v * vstride + i] = s[v * VS];
-        }
-        __syncthreads();
+__device__ __forceinline__ int level_of(const SweepArgs<float>& a, int item) {
+    int l = 0;
+    while (l + 1 < a.n_levels && item >= a.lv[l + 1].item0) ++l;
+    return l;
+}
+
+// Threads 0..26 and 32..58 of the block.
+__device__ __forceinline__ void build_tab(ItemTab& t, const SweepArgs<float>& a, int item) {
+    const int l = level_of(a, item);
+    const LevelArgs<float>& L = a.lv[l];
+    const int g = item - L.item0;
+    const int tid = threadIdx.x;
+    if (tid < 27) region_entry(L.nbr, g, tid, t.src, t.mask);
+    if (tid >= 32 && tid < 59 && L.parent != nullptr)
+        region_entry(L.nbrc, L.parent[g] >> 3, tid - 32, t.csrc, t.cmask);
+    if (tid == 0) {
+        t.item = item;
+        t.level = l;
+        t.g = g;
+        t.par = L.parent != nullptr ? L.parent[g] : -1;
     }
 }
 
-template <int NT, int ORDER, int LIM>
-static cudaError_t launch_one(const SweepArgs<float>& a, int grid, cudaStream_t st) {
-    auto k = k_sweep_f32<NT, ORDER, LIM>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_F32);
-    if (e != cudaSuccess) return e;
-    k<<<grid, NT, SMEM_F32, st>>>(a);
-    return cudaGetLastError();
+__device__ __forceinline__ void prolong_cell(const LevelArgs<float>& L, const ItemTab& t, int x, int y,
+                                             int z, float val[NV]) {
+    const int lp = t.par & 7;
+    prolong<float>(L.uc, (size_t)L.n_groups_c * 8 * 512, t.csrc, t.cmask, lp & 1, (lp >> 1) & 1,
+                   (lp >> 2) & 1, x, y, z, val);
 }
 
-template <int NT>
-static cudaError_t launch_nt(const SweepArgs<float>& a, int order, int lim, int grid, cudaStream_t st) {
-    if (order == 0) return lim == 0 ? launch_one<NT, 0, 0>(a, grid, st) : launch_one<NT, 0, 1>(a, grid, st);
-    return lim == 0 ? launch_one<NT, 1, 0>(a, grid, st) : launch_one<NT, 1, 1>(a, grid, st);
+// One padded x-row (yp, zp) of the block of item t.  SEG bit 0: the 16
+// centre cells (x in [0,16)); bit 1: the 3 + 3 edge cells.  Every cell lies
+// in an aligned quad of a patch row of its source group, so the centre is
+// four 16-byte loads per variable and each edge one.  Outflow edges repeat
+// the centre's edge cell (zero gradient); cells of coarse regions are
+// interpolated one by one.
+template <int SEG>
+__device__ __forceinline__ void gather_row(float* sm, const SweepArgs<float>& a, const ItemTab& t,
+                                           int yp, int zp) {
+    const LevelArgs<float>& L = a.lv[t.level];
+    const size_t vstride = (size_t)L.n_groups * 8 * 512;
+    float* d = sm + (zp * PD + yp) * XP;
+    const int y = yp - NG, z = zp - NG;
+    int xc = 0, yc = y, zc = z;
+    const int sc = resolve(t.src, t.mask, xc, yc, zc);
+    const size_t offc = sc >= 0 ? cell_offset(sc, 0, yc, zc) : 0;
+    if (SEG & 1) {
+        if (sc >= 0) {
+            float4 c[NV][4];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const float* p = L.u + v * vstride + offc;
+                c[v][0] = ldg4(p);
+                c[v][1] = ldg4(p + 4);
+                c[v][2] = ldg4(p + 512);       // patch px = 1
+                c[v][3] = ldg4(p + 516);
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                float* q = d + v * VS + NG;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    q[4 * j + 0] = c[v][j].x;
+                    q[4 * j + 1] = c[v][j].y;
+                    q[4 * j + 2] = c[v][j].z;
+                    q[4 * j + 3] = c[v][j].w;
+                }
+            }
+        } else {
+            for (int x = 0; x < GS; ++x) {
+                float val[NV];
+                prolong_cell(L, t, x, y, z, val);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) d[v * VS + NG + x] = val[v];
+            }
+        }
+    }
+    if (SEG & 2) {
+        const int rb = (region_of(z) + 1) * 9 + (region_of(y) + 1) * 3;
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const int o = side == 0 ? 0 : NG + GS;       // first padded cell of the edge
+            if (t.mask[rb + 2 * side] & 1) {
+                // outflow along x: the centre's cell at x = 0 or 15, three times
+                float val[NV];
+                if (sc >= 0) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) val[v] = L.u[v * vstride + offc + (side ? 512 + 7 : 0)];
+                } else {
+                    prolong_cell(L, t, side ? GS - 1 : 0, y, z, val);
+                }
+#pragma unroll
+                for (int v = 0; v < NV; ++v) d[v * VS + o] = d[v * VS + o + 1] = d[v * VS + o + 2] = val[v];
+                continue;
+            }
+            int xs = side ? GS : -1, ys = y, zs = z;
+            const int se = resolve(t.src, t.mask, xs, ys, zs);
+            if (se >= 0) {
+                // x = 12..15 of the -x neighbour's px = 1 row, or x = 0..3 of the +x one
+                const size_t off = cell_offset(se, 0, ys, zs) + (side ? 0 : 512 + 4);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const float4 q = ldg4(L.u + v * vstride + off);
+                    if (side == 0) {
+                        d[v * VS + 0] = q.y;
+                        d[v * VS + 1] = q.z;
+                        d[v * VS + 2] = q.w;
+                    } else {
+                        d[v * VS + 19] = q.x;
+                        d[v * VS + 20] = q.y;
+                        d[v * VS + 21] = q.z;
+                    }
+                }
+            } else {
+                for (int k = 0; k < NG; ++k) {
+                    float val[NV];
+                    prolong_cell(L, t, side ? GS + k : k - NG, y, z, val);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) d[v * VS + o + k] = val[v];
+                }
+            }
+        }
+    }
+}
+
+// Row sets of the pipelined gather of the next item, chosen so that each
+// set only writes cells the current item no longer reads:
+//   xyz: A during sweep 2: x-edges of all rows; B during sweep 3: centres of
+//        rows outside [3,19) in y; C during the store: centres of rows
+//        outside [3,19) in z (inside in y); D after the store: centres of
+//        the 16x16 interior rows.
+//   zyx: A: full rows outside [3,19) in z; B: full rows inside in z,
+//        outside in y; C: x-edges of the interior rows; D: their centres.
+__device__ __forceinline__ int ghost_row(int q) { return q < NG ? q : q + GS; }   // 0..5 -> 0,1,2,19,20,21
+
+template <int ORDER, int PH>
+__device__ __forceinline__ void gather_set(float* sm, const SweepArgs<float>& a, const ItemTab& t,
+                                           int t0, int stride) {
+    constexpr int N = ORDER == 0 ? (PH == 0 ? PD * PD : PH == 1 ? 6 * PD : PH == 2 ? 6 * GS : GS * GS)
+                                 : (PH == 0 ? 6 * PD : PH == 1 ? 6 * GS : GS * GS);
+    for (int r = t0; r < N; r += stride) {
+        int yp, zp;
+        if (ORDER == 0) {
+            if (PH == 0) { yp = r % PD; zp = r / PD; }
+            else if (PH == 1) { yp = ghost_row(r % 6); zp = r / 6; }
+            else if (PH == 2) { yp = NG + r % GS; zp = ghost_row(r / GS); }
+            else { yp = NG + r % GS; zp = NG + r / GS; }
+            if (PH == 0) gather_row<2>(sm, a, t, yp, zp);
+            else gather_row<1>(sm, a, t, yp, zp);
+        } else {
+            if (PH == 0) { yp = r % PD; zp = ghost_row(r / PD); }
+            else if (PH == 1) { yp = ghost_row(r % 6); zp = NG + r / 6; }
+            else { yp = NG + r % GS; zp = NG + r / GS; }
+            if (PH <= 1) gather_row<3>(sm, a, t, yp, zp);
+            else if (PH == 2) gather_row<2>(sm, a, t, yp, zp);
+            else gather_row<1>(sm, a, t, yp, zp);
+        }
+    }
+}
+
+// Interior 16^3 -> u_out: one item per (variable, interior x-row), two
+// aligned 16-byte stores per patch row.
+__device__ __forceinline__ void store_rows(const float* sm, const LevelArgs<float>& L, int g, int t0,
+                                           int stride) {
+    const size_t vstride = (size_t)L.n_groups * 8 * 512;
+    for (int it = t0; it < NV * GS * GS; it += stride) {
+        const int v = it / (GS * GS), r = it % (GS * GS);
+        const int y = r % GS, z = r / GS;
+        const float* s = sm + v * VS + ((z + NG) * PD + (y + NG)) * XP + NG;
+        float* o = L.u_out + v * vstride + cell_offset(g, 0, y, z);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float4 q = make_float4(s[4 * j], s[4 * j + 1], s[4 * j + 2], s[4 * j + 3]);
+            *reinterpret_cast<float4*>(o + (j >> 1) * 512 + (j & 1) * 4) = q;
+        }
+    }
+}
+
+// Persistent kernel.  NT = 512 threads (16 warps), one CTA per SM.
+//   sweep 1: all warps;
+//   sweep 2: 352 columns on warps 0..10, warps 11..15 gather set A of the
+//            next item;
+//   sweep 3: 256 columns on warps 0..7, warps 8..15 gather set B;
+//   store:   warps 0..7 write the interior, warps 8..15 gather set C;
+//   then all warps gather set D (the next item's interior centres).
+// The first item of each CTA is gathered whole.  Work items come from an
+// atomic counter, one item ahead, whose interior is prefetched into L2.
+constexpr int NT_F32 = 512;
+
+template <int ORDER, int LIM>
+__global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> args) {
+    extern __shared__ float sm[];
+    ItemTab* tab = reinterpret_cast<ItemTab*>(sm + NV * VS);     // [2]
+    int* s_item = reinterpret_cast<int*>(tab + 2);               // current, next
+    const int tid = threadIdx.x;
+
+    if (tid == 0) {
+        s_item[0] = atomicAdd(args.queue, 1);
+        s_item[1] = atomicAdd(args.queue, 1);
+    }
+    __syncthreads();
+    if (s_item[0] >= args.total) return;
+    int slot = 0;
+    build_tab(tab[0], args, s_item[0]);
+    __syncthreads();
+    for (int r = tid; r < PD * PD; r += NT_F32) gather_row<3>(sm, args, tab[0], r % PD, r / PD);
+
+    for (;;) {
+        const int next = s_item[1];
+        const bool has_next = next < args.total;
+        if (has_next) {
+            build_tab(tab[slot ^ 1], args, next);
+            if (tid == 0) {
+                const LevelArgs<float>& Ln = args.lv[level_of(args, next)];
+                const size_t vs = (size_t)Ln.n_groups * 8 * 512;
+                const int gn = next - Ln.item0;
+                const float* b = Ln.u + ((size_t)gn << 12);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) prefetch_l2(b + v * vs, CELLS_PG * sizeof(float));
+            }
+        }
+        __syncthreads();
+        const ItemTab& cur = tab[slot];
+        const ItemTab& nxt = tab[slot ^ 1];
+        const LevelArgs<float>& L = args.lv[cur.level];
+        float* fg = L.flux ? L.flux + (size_t)cur.g * FLUX_PG : nullptr;
+
+        sweep<ORDER, 0, LIM>(sm, L.lam, args.gamma, args.gm1, fg, NT_F32);
+        __syncthreads();
+        if (tid < 11 * 32) sweep<ORDER, 1, LIM>(sm, L.lam, args.gamma, args.gm1, fg, 11 * 32);
+        else if (has_next) gather_set<ORDER, 0>(sm, args, nxt, tid - 11 * 32, NT_F32 - 11 * 32);
+        __syncthreads();
+        if (tid < 8 * 32) sweep<ORDER, 2, LIM>(sm, L.lam, args.gamma, args.gm1, fg, 8 * 32);
+        else if (has_next) gather_set<ORDER, 1>(sm, args, nxt, tid - 8 * 32, NT_F32 - 8 * 32);
+        __syncthreads();
+        if (tid < 8 * 32) store_rows(sm, L, cur.g, tid, 8 * 32);
+        else if (has_next) gather_set<ORDER, 2>(sm, args, nxt, tid - 8 * 32, NT_F32 - 8 * 32);
+        if (tid == 0) {
+            s_item[0] = next;
+            s_item[1] = has_next ? atomicAdd(args.queue, 1) : next;
+        }
+        __syncthreads();
+        if (!has_next) break;
+        slot ^= 1;
+        gather_set<ORDER, 3>(sm, args, tab[slot], tid, NT_F32);
+    }
+}
+
+template <int ORDER, int LIM>
+static cudaError_t launch_one(const SweepArgs<float>& a, int grid, cudaStream_t st) {
+    auto k = k_sweep_f32<ORDER, LIM>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_F32);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NT_F32, SMEM_F32, st>>>(a);
+    return cudaGetLastError();
 }
 
 size_t sweep_f32_smem() { return SMEM_F32; }
 
 cudaError_t launch_sweep_f32(const SweepArgs<float>& a, int order, int lim, int threads, int grid,
                              cudaStream_t st) {
-    switch (threads) {
-        case 256: return launch_nt<256>(a, order, lim, grid, st);
-        case 384: return launch_nt<384>(a, order, lim, grid, st);
-        case 512: return launch_nt<512>(a, order, lim, grid, st);
-        default: return cudaErrorInvalidValue;
-    }
+    if (threads != NT_F32) return cudaErrorInvalidValue;
+    if (order == 0) return lim == 0 ? launch_one<0, 0>(a, grid, st) : launch_one<0, 1>(a, grid, st);
+    return lim == 0 ? launch_one<1, 0>(a, grid, st) : launch_one<1, 1>(a, grid, st);
 }
 
 }  // namespace gh

@@ -316,7 +316,8 @@ def test_bad_maps_and_arguments_are_rejected():
         B.gamer_hydro_advance_all(S.h, D2, 0.01)
     assert e.value.code == B.GAMER_ERR_MAP
     D3 = B.DeviceHierarchy(H, st, torch.float32)
-    D3.u_out[0] = D3.u[0]
+    B.gamer_hydro_advance(S.h, D3, 0, 0.0)      # version validated with good pointers
+    D3.u_out[0] = D3.u[0]                        # then alias u_out with u on the same version
     D3._refresh()
     with pytest.raises(B.GamerError) as e:
         B.gamer_hydro_advance(S.h, D3, 0, 0.01)
