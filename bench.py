@@ -127,7 +127,8 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "20"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.5)     # let nvidia-smi start sampling before the timed region
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -158,23 +159,22 @@ class ClockSampler:
 
 def cpu_oracle_rate(H, states, seconds, threads):
     """Oracle (plain FP64 C, OpenMP over patch groups) on a bounded sample of
-    the workload's patch groups: cell-updates/s and the sample description."""
+    the workload: sweep sets of level 0, repeated until about `seconds` of
+    CPU work.  Returns cell-updates/s, the sample description and seconds."""
     import oracle
     oracle.set_threads(threads)
     O = oracle.OracleLevels(H, [np.asarray(s, dtype=np.float64) for s in states])
     dt = O.cfl_dt(GAMMA, CFL)
-    lv = 0
-    n = H.levels[lv].n_groups
-    probe = min(n, max(threads, 8))
-    t0 = time.perf_counter()
-    O.advance_level(lv, GAMMA, dt, 0, groups=np.arange(probe))
-    t1 = time.perf_counter() - t0
-    count = int(min(n, max(probe, probe * seconds / max(t1, 1e-6))))
-    groups = np.arange(count)
-    t0 = time.perf_counter()
-    O.advance_level(lv, GAMMA, dt, 0, groups=groups)
-    el = time.perf_counter() - t0
-    return count * 4096 / el, f"{count} of {n} patch groups of level {lv}, one xyz sweep set", el
+    n = H.levels[0].n_groups
+    groups = np.arange(n)
+    done, el, k = 0, 0.0, 0
+    while el < seconds:
+        t0 = time.perf_counter()
+        O.advance_level(0, GAMMA, dt, k % 2, groups=groups)
+        el += time.perf_counter() - t0
+        done += n
+        k += 1
+    return done * 4096 / el, f"{k} sweep sets of all {n} patch groups of level 0", el
 
 
 # ------------------------------------------------------------ reference arm
@@ -222,6 +222,12 @@ def run_reference(args, rank, world):
 
 # ------------------------------------------------------------ our arm
 
+def _timing_event(torch):
+    e = torch.cuda.Event(enable_timing=True)
+    e.record()          # materialise the underlying cudaEvent_t
+    return e
+
+
 def run_ours(args, rank, world, dist):
     import torch
     from paper_0907_3390_gb300 import binding as B
@@ -242,45 +248,44 @@ def run_ours(args, rank, world, dist):
     D = B.DeviceHierarchy(H, st, torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    dt = B.gamer_hydro_cfl_dt(S.h, D, CFL)
-    state = {"dt": dt}
-
-    def step(ev=None):
-        if ev is not None:
-            ev[0].record(stream)
-        B.gamer_hydro_advance_all(S.h, D, state["dt"])
-        if ev is not None:
-            ev[1].record(stream)
+    def step():
+        B.gamer_hydro_step(S.h, D, CFL)      # sweeps + CFL dt + check, one graph replay
         D.swap()
-        dtn, sums, nb = B.gamer_hydro_diagnose(S.h, D, CFL)
-        if B.gamer_hydro_get_parity(S.h, 0) == 0:   # next call is xyz: new dt (held for zyx)
-            state["dt"] = dtn
-        return sums, nb
 
+    s0, _ = B.gamer_hydro_check(S.h, D)
+    clocks = None if args.quick else ClockSampler(local)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    sums0, _ = step()
 
-    clocks = None if args.quick else ClockSampler(local)
+    # timed region: K whole steps, each bracketed by events on the launch
+    # stream, L2 flushed before each
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
     torch.cuda.synchronize()
-    wall0 = time.perf_counter()
-    n_bad = 0
     for s in range(args.steps):
         flush.fill_(float(s))                       # evict L2 (outside the timed interval)
         ev[s][0].record(stream)
-        sums, nb = step(kev[s])
+        step()
         ev[s][1].record(stream)
-        n_bad += nb
     torch.cuda.synchronize()
     barrier()
-    wall = time.perf_counter() - wall0
     clk = clocks.stop() if clocks else None
+    dt_used, dt_next, sums, n_bad = B.gamer_hydro_step_result(S.h)
     step_ms = sum(a.elapsed_time(b) for a, b in ev)
-    kern_ms = [a.elapsed_time(b) for a, b in kev]
+
+    # the dominant kernel: the same steps again with profiling events around
+    # the sweep launch (launched directly, events cannot be timed in graphs)
+    kev = (_timing_event(torch), _timing_event(torch))
+    torch.cuda.synchronize()
+    B.gamer_hydro_set_profiling(S.h, kev[0], kev[1])
+    kern_ms = []
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        step()
+        torch.cuda.synchronize()
+        kern_ms.append(kev[0].elapsed_time(kev[1]))
+    B.gamer_hydro_set_profiling(S.h, None, None)
     t_local = step_ms / 1e3
     if dist is not None:
         t = torch.tensor([t_local], dtype=torch.float64, device=dev)
@@ -298,29 +303,27 @@ def run_ours(args, rank, world, dist):
     res["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                        "frac": achieved / hbm, "peak_kind": f"{peak_kind} copy bandwidth",
                        "traffic": None if tpc is None else tpc * cells,
-                       "kernel": "k_sweep_f32 (gather + 3 sweeps + store, one persistent launch)",
+                       "kernel": "k_sweep_f32 (gather + 3 sweeps + store + fused diagnostics, one persistent launch)",
                        "kernel_ms": 1e3 * k_avg, "algorithmic_bytes": BYTES_PER_CELL_F32 * cells}
     res["clocks"] = clk
-    conservation = None
-    if not args.quick:
-        conservation = float(np.max(np.abs(sums - sums0) / (np.abs(sums0) + 1e-30)))
-
+    res["conservation_drift_rel"] = float(np.max(np.abs(sums - s0) / (np.abs(s0) + 1e-30)))
+    res["n_bad"] = n_bad
     extras = {}
     if not args.quick and rank == 0:
         extras = run_extras(args, B, torch, H, st, cells, dev, stream)
     S.close()
-    return res, extras, cells, n_bad, conservation, desc
+    return res, extras, cells, desc
 
 
 def run_extras(args, B, torch, H, st, cells, dev, stream):
     out = {}
-    # ---- e2e through the C ABI with host buffers: H2D of the state, the
-    # step, D2H of the new state, every step
+    # ---- e2e through the C ABI with host buffers: every step copies the
+    # state in from pinned host memory, takes the step (the graph also
+    # copies the step result to the host) and copies the new state out
     S = B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP32, stream=stream)
     D = B.DeviceHierarchy(H, st, torch.float32, device=dev)
     host_in = [x.cpu().pin_memory() for x in D.u]
-    host_out = [torch.empty_like(x) for x in host_in]
-    dt = B.gamer_hydro_cfl_dt(S.h, D, CFL)
+    host_out = [torch.empty_like(x).pin_memory() for x in host_in]
     n_e2e = max(3, min(args.steps, 10))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for it in range(2 + n_e2e):
@@ -329,22 +332,22 @@ def run_extras(args, B, torch, H, st, cells, dev, stream):
             e0.record(stream)
         for l in range(len(D.u)):
             D.u[l].copy_(host_in[l], non_blocking=True)
-        B.gamer_hydro_advance_all(S.h, D, dt)
+        B.gamer_hydro_step(S.h, D, CFL)
         D.swap()
-        dtn, sums, nb = B.gamer_hydro_diagnose(S.h, D, CFL)
         for l in range(len(D.u)):
             host_out[l].copy_(D.u[l], non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
+    B.gamer_hydro_step_result(S.h)
     ms = e0.elapsed_time(e1) / n_e2e
     nbytes = sum(x.numel() * 4 for x in host_in)
     out["e2e"] = {"value": cells / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                  "d2h_bytes_per_step": nbytes + 8 * 7}
+                  "d2h_bytes_per_step": nbytes + 96}
     S.close()
 
-    # ---- plain FP64 GPU path (one block per patch group) and the per-field
-    # L1 error of one FP32 sweep set against it (the FP64 path is
-    # bit-identical to the FP64 oracle in the parity tests)
+    # ---- plain FP64 GPU path (one block per patch group, same whole-step
+    # API) and the per-field L1 error of one FP32 sweep set against it (the
+    # FP64 path is bit-identical to the FP64 oracle in the parity tests)
     S64 = B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP64, stream=stream)
     D64 = B.DeviceHierarchy(H, st, torch.float64, device=dev)
     dt = B.gamer_hydro_cfl_dt(S64.h, D64, CFL)
@@ -357,16 +360,18 @@ def run_extras(args, B, torch, H, st, cells, dev, stream):
     scale = ref.reshape(5, -1).abs().max(dim=1).values
     l1 = ((got - ref).reshape(5, -1).abs().mean(dim=1) / scale).cpu().numpy()
     n64 = 3
+    B.gamer_hydro_step(S64.h, D64, CFL)
+    D64.swap()
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(n64):
-        B.gamer_hydro_advance_all(S64.h, D64, dt)
+        B.gamer_hydro_step(S64.h, D64, CFL)
         D64.swap()
     e1.record(stream)
     torch.cuda.synchronize()
     ms64 = e0.elapsed_time(e1) / n64
     out["fp64_plain"] = {"value": cells / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
-                         "note": "advance only, one thread block per patch group, FP64 throughout"}
+                         "note": "whole step, one thread block per patch group, FP64 throughout"}
     out["l1_rel_err_fp32_vs_fp64"] = {"fields": ["rho", "mx", "my", "mz", "e"], "value": [float(x) for x in l1],
                                       "after": "one sweep set"}
     S64.close()
@@ -395,7 +400,7 @@ def main():
         if dist is not None:
             dist.destroy_process_group()
         return rc
-    res, extras, cells, n_bad, cons, desc = run_ours(args, rank, world, dist)
+    res, extras, cells, desc = run_ours(args, rank, world, dist)
     if rank == 0:
         steps = args.steps
         line = {
@@ -403,16 +408,16 @@ def main():
             "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": desc, "cells_per_gpu": cells, "precision": "FP32 batched, FP64 reductions",
-                       "step": "advance_all (gather + 3 sweeps) + diagnose (CFL dt, sums, positivity)",
+                       "step": "gamer_hydro_step: gather + 3 sweeps + CFL dt + conservation/positivity check "
+                               "(one CUDA graph: persistent sweep kernel with fused diagnostics, final reduction)",
                        "l2": "flushed before every timed step (256 MiB write, outside the timed interval)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "roofline": res["roofline"],
-            "gpu_launches": 3 * steps,
+            "gpu_launches": 2 * steps,
             "clocks": res["clocks"],
-            "n_bad_cells": n_bad,
+            "n_bad_cells": res["n_bad"],
+            "conservation_drift_rel": res["conservation_drift_rel"],
         }
-        if cons is not None:
-            line["conservation_drift_rel"] = cons
         for k in ("e2e", "cpu_baseline", "fp64_plain", "l1_rel_err_fp32_vs_fp64"):
             if k in extras:
                 line[k] = extras[k]

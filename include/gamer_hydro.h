@@ -144,10 +144,33 @@ int gamer_hydro_fixup(gamer_hydro_t h, const gamer_hierarchy_t *H, int level,
 /* Whole step of the level evolution with a uniform dt: every level
  * advanced (the FP32 handle uses ONE persistent launch whose device work
  * queue spans the patch groups of all levels), then the fix-ups from the
- * finest level down, all captured once per (hierarchy version, pointers,
- * parity) in a CUDA graph and replayed.  Flips every level's parity.
- * Asynchronous.  The caller swaps u and u_out of every level afterwards. */
+ * finest level down.  Flips every level's parity (all levels must share
+ * it, else GAMER_ERR_STATE).  Asynchronous.  The caller swaps u and u_out
+ * of every level afterwards. */
 int gamer_hydro_advance_all(gamer_hydro_t h, const gamer_hierarchy_t *H, double dt);
+
+/* One whole step with the time step kept on the device: the sweep sets and
+ * fix-ups of gamer_hydro_advance_all with the handle's device dt, then the
+ * diagnostics of the new state (per-group exact speed maxima, FP64 leaf
+ * sums, bad-cell count; fused into the sweep launch for single-level FP32
+ * hierarchies) and the dt of the next step from Eq. CFL with factor cfl.
+ * Following the forward/backward sweep pairing of Sec. 2.2 the new dt is
+ * taken only when the next step is an xyz step; a zyx step reuses the dt of
+ * the xyz step before it.  The first call on a hierarchy version (or after
+ * any call that set dt from the host) computes dt from the current state
+ * first.  The sequence is captured once per (hierarchy version, u/u_out
+ * pointers, parity, cfl) as a CUDA graph and replayed on the handle's
+ * stream: no host round trip per step.  Asynchronous; the caller swaps u
+ * and u_out afterwards and may read the result with
+ * gamer_hydro_step_result. */
+int gamer_hydro_step(gamer_hydro_t h, const gamer_hierarchy_t *H, double cfl);
+
+/* Result of the last gamer_hydro_step: the dt it used, the dt the next
+ * step will use, the leaf sums of u * dh^3 and the bad-cell count of the
+ * new state.  Waits for that step.  Any output pointer may be NULL.
+ * GAMER_ERR_STATE if no step has completed. */
+int gamer_hydro_step_result(gamer_hydro_t h, double *dt_used, double *dt_next, double sums[5],
+                            int64_t *n_bad);
 
 /* Conservation and positivity check over leaf cells (patches whose child
  * is -1) of every level's u: sums[v] = sum of u_v * dh^3 (FP64,
@@ -160,6 +183,15 @@ int gamer_hydro_check(gamer_hydro_t h, const gamer_hierarchy_t *H, double sums[5
  * (either output pointer may be NULL).  Synchronous. */
 int gamer_hydro_diagnose(gamer_hydro_t h, const gamer_hierarchy_t *H, double cfl,
                          double *dt_out, double sums[5], int64_t *n_bad);
+
+/* Profiling hook: CUDA events (cudaEvent_t, created with timing enabled)
+ * that every later advance_all / step records immediately before and after
+ * its sweep launches, so the caller can time the dominant kernel with
+ * cudaEventElapsedTime.  While events are set, gamer_hydro_step launches
+ * its sequence directly instead of replaying a graph (events recorded
+ * inside a graph cannot be timed).  Both NULL turns it off.  The events
+ * stay owned by the caller and must outlive their use. */
+int gamer_hydro_set_profiling(gamer_hydro_t h, void *ev_before, void *ev_after);
 
 /* Message of the last failed call on this handle ("" if none).  With a NULL
  * handle, the message of the last failed gamer_hydro_create on this thread.

@@ -25,7 +25,8 @@ EXPORTS = [
     "gamer_hydro_create", "gamer_hydro_destroy", "gamer_hydro_set_stream",
     "gamer_hydro_set_parity", "gamer_hydro_get_parity", "gamer_hydro_cfl_dt",
     "gamer_hydro_advance", "gamer_hydro_fixup", "gamer_hydro_advance_all",
-    "gamer_hydro_check", "gamer_hydro_diagnose", "gamer_hydro_last_error",
+    "gamer_hydro_check", "gamer_hydro_diagnose", "gamer_hydro_step", "gamer_hydro_step_result",
+    "gamer_hydro_set_profiling", "gamer_hydro_last_error",
 ]
 
 
@@ -77,6 +78,9 @@ def load(build_if_needed: bool = True) -> C.CDLL:
         L.gamer_hydro_advance_all.argtypes = [H, hp, C.c_double]
         L.gamer_hydro_check.argtypes = [H, hp, dp, C.POINTER(C.c_int64)]
         L.gamer_hydro_diagnose.argtypes = [H, hp, C.c_double, dp, dp, C.POINTER(C.c_int64)]
+        L.gamer_hydro_step.argtypes = [H, hp, C.c_double]
+        L.gamer_hydro_step_result.argtypes = [H, dp, dp, dp, C.POINTER(C.c_int64)]
+        L.gamer_hydro_set_profiling.argtypes = [H, vp, vp]
         L.gamer_hydro_last_error.argtypes = [H]
         L.gamer_hydro_last_error.restype = C.c_char_p
         for name in EXPORTS:
@@ -152,6 +156,25 @@ def gamer_hydro_diagnose(h, H, cfl: float):
     nb = C.c_int64()
     _check(h, load().gamer_hydro_diagnose(h, H.struct(), cfl, C.byref(dt), sums, C.byref(nb)))
     return dt.value, np.array(sums[:]), int(nb.value)
+
+
+def gamer_hydro_step(h, H, cfl: float) -> None:
+    _check(h, load().gamer_hydro_step(h, H.struct(), cfl))
+
+
+def gamer_hydro_step_result(h):
+    """(dt_used, dt_next, sums[5], n_bad) of the last gamer_hydro_step."""
+    du, dn = C.c_double(), C.c_double()
+    sums = (C.c_double * 5)()
+    nb = C.c_int64()
+    _check(h, load().gamer_hydro_step_result(h, C.byref(du), C.byref(dn), sums, C.byref(nb)))
+    return du.value, dn.value, np.array(sums[:]), int(nb.value)
+
+
+def gamer_hydro_set_profiling(h, ev_before, ev_after) -> None:
+    """ev_*: torch.cuda.Event(enable_timing=True) or raw cudaEvent_t, or None."""
+    raw = [None if e is None else getattr(e, "cuda_event", e) for e in (ev_before, ev_after)]
+    _check(h, load().gamer_hydro_set_profiling(h, *[C.c_void_p(r) if r else None for r in raw]))
 
 
 def gamer_hydro_last_error(h) -> str:

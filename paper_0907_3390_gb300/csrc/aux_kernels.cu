@@ -16,6 +16,10 @@ namespace gh {
 // z-, z+.
 template <typename T>
 __global__ void __launch_bounds__(512) k_fixup(const FixArgs<T> a) {
+    __shared__ double s_lam;
+    if (threadIdx.x == 0) s_lam = *a.dt / a.dh;   // coarse lambda = dt / dh
+    __syncthreads();
+    const T lam = (T)s_lam;
     const int P = a.list[blockIdx.x];
     const int g = P >> 3, lp = P & 7;
     const int pc[3] = {lp & 1, (lp >> 1) & 1, (lp >> 2) & 1};
@@ -71,8 +75,8 @@ __global__ void __launch_bounds__(512) k_fixup(const FixArgs<T> a) {
                 const T* ff = a.flux_f + ((((size_t)gfq * 3 + ax) * 3 + plane_f) * NV + v) * 256;
                 const T Gf = T(0.25) * (((ff[(2 * b2) * GS + 2 * b1] + ff[(2 * b2) * GS + 2 * b1 + 1]) +
                                          ff[(2 * b2 + 1) * GS + 2 * b1]) + ff[(2 * b2 + 1) * GS + 2 * b1 + 1]);
-                if (s > 0) val[v] = val[v] + a.lam * (Gc - Gf);
-                else val[v] = val[v] - a.lam * (Gc - Gf);
+                if (s > 0) val[v] = val[v] + lam * (Gc - Gf);
+                else val[v] = val[v] - lam * (Gc - Gf);
             }
             touched = true;
         }
@@ -108,11 +112,7 @@ __device__ __forceinline__ void speed_pressure(const double u[NV], double g, dou
 }
 __device__ __forceinline__ void speed_pressure(const float u[NV], float g, float gm1, float& s,
                                                float& P) {
-    const float ri = __fdividef(1.0f, u[0]);
-    const float m2 = fmaf(u[1], u[1], fmaf(u[2], u[2], u[3] * u[3]));
-    P = gm1 * fmaf(-0.5f * ri, m2, u[4]);
-    const float cs = sqrtf(g * fmaxf(P, 0.0f) * ri);
-    s = cs + fmaxf(fmaxf(fabsf(u[1]), fabsf(u[2])), fabsf(u[3])) * ri;
+    speed_pressure_f32(u, g, gm1, s, P);
 }
 
 // Error-free accumulation for the FP32 path: a double-float (hi, lo) pair
@@ -256,5 +256,111 @@ cudaError_t launch_diag(const DiagArgs<T>& a, int total, cudaStream_t st) {
 }
 template cudaError_t launch_diag<float>(const DiagArgs<float>&, int, cudaStream_t);
 template cudaError_t launch_diag<double>(const DiagArgs<double>&, int, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_diag_groups(const DiagArgs<T>& a, int total, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    k_diag<T><<<total, NT_DIAG, 0, st>>>(a);
+    return cudaGetLastError();
+}
+template cudaError_t launch_diag_groups<float>(const DiagArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_diag_groups<double>(const DiagArgs<double>&, int, cudaStream_t);
+
+// ------------------------------------------------------------ whole step
+
+__global__ void k_set_dt(double* slot, double dt) { *slot = dt; }
+
+cudaError_t launch_set_dt(double* slot, double dt, cudaStream_t st) {
+    k_set_dt<<<1, 1, 0, st>>>(slot, dt);
+    return cudaGetLastError();
+}
+
+struct LevelMeta {
+    int item0[MAXLEV];
+    int n[MAXLEV];
+    double dh[MAXLEV];
+    int n_levels;
+};
+
+// One block: per level, the per-group results in fixed order (strided
+// partials, fixed tree); then Eq. CFL dt = cfl * min_l dh_l / s_l in FP64
+// and the leaf sums times dh^3, level by level.  *dt becomes the new value
+// when update_dt is set (the next step is an xyz step), otherwise it is
+// held (reading of Sec. 2.2: one dt for a forward and backward sweep).
+__global__ void __launch_bounds__(NT_FIN) k_step_final(const LevelMeta m, const unsigned long long* pg_max,
+                                                      const double* pg_sum, const int* pg_bad, double cfl,
+                                                      double* dt, int update_dt, StepOut* out) {
+    __shared__ double s_sum[NV][NT_FIN];
+    __shared__ unsigned long long s_max[NT_FIN];
+    __shared__ long long s_bad[NT_FIN];
+    double tot[NV] = {0, 0, 0, 0, 0};
+    double dtc = INFINITY;
+    long long nb = 0;
+    const double dt_used = *dt;
+    for (int l = 0; l < m.n_levels; ++l) {
+        double sum[NV] = {0, 0, 0, 0, 0};
+        unsigned long long mx = 0ull;
+        long long bad = 0;
+        for (int i = threadIdx.x; i < m.n[l]; i += NT_FIN) {
+            const int it = m.item0[l] + i;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sum[v] += pg_sum[(size_t)it * NV + v];
+            mx = max(mx, pg_max[it]);
+            bad += pg_bad[it];
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) s_sum[v][threadIdx.x] = sum[v];
+        s_max[threadIdx.x] = mx;
+        s_bad[threadIdx.x] = bad;
+        __syncthreads();
+        for (int w = NT_FIN / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) s_sum[v][threadIdx.x] += s_sum[v][threadIdx.x + w];
+                s_max[threadIdx.x] = max(s_max[threadIdx.x], s_max[threadIdx.x + w]);
+                s_bad[threadIdx.x] += s_bad[threadIdx.x + w];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0 && m.n[l] > 0) {
+            const double dV = m.dh[l] * m.dh[l] * m.dh[l];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) tot[v] += s_sum[v][0] * dV;
+            const double s = __longlong_as_double((long long)s_max[0]);
+            const double d = m.dh[l] / s;
+            if (d < dtc || d != d) dtc = d;
+            nb += s_bad[0];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double dnew = cfl * dtc;
+        out->dt_used = dt_used;
+        out->dt_cfl = dnew;
+        out->dt_next = update_dt ? dnew : dt_used;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) out->sum[v] = tot[v];
+        out->n_bad = nb;
+        out->steps += 1;
+        if (update_dt) *dt = dnew;
+    }
+}
+
+cudaError_t launch_step_final(const DiagArgs<float>& a32, const DiagArgs<double>& a64, bool fp64,
+                              const double* dh, double cfl, double* dt, int update_dt, StepOut* out,
+                              cudaStream_t st) {
+    LevelMeta m;
+    m.n_levels = fp64 ? a64.n_levels : a32.n_levels;
+    for (int l = 0; l < m.n_levels; ++l) {
+        m.item0[l] = fp64 ? a64.lv[l].item0 : a32.lv[l].item0;
+        m.n[l] = fp64 ? a64.lv[l].n_groups : a32.lv[l].n_groups;
+        m.dh[l] = dh[l];
+    }
+    const unsigned long long* pm = fp64 ? a64.pg_max : a32.pg_max;
+    const double* ps = fp64 ? a64.pg_sum : a32.pg_sum;
+    const int* pb = fp64 ? a64.pg_bad : a32.pg_bad;
+    k_step_final<<<1, NT_FIN, 0, st>>>(m, pm, ps, pb, cfl, dt, update_dt, out);
+    return cudaGetLastError();
+}
 
 }  // namespace gh

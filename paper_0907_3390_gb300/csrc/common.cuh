@@ -35,7 +35,15 @@ struct LevelArgs {
     int n_groups_c;
     int item0;          // first work item of this level in a multi-level launch
     int pad_;
-    T lam;              // dt / dh of this level
+    double dh;          // cell width; lambda = dt / dh is formed on the device in FP64
+};
+
+// Per-group diagnostic sinks (exact max of the signal speed, leaf sums of
+// the conserved variables, count of bad leaf cells), indexed by work item.
+struct DiagSink {
+    unsigned long long* pg_max;
+    double* pg_sum;     // [item][5]
+    int* pg_bad;
 };
 
 template <typename T>
@@ -44,6 +52,8 @@ struct SweepArgs {
     int n_levels;
     int total;          // work items (patch groups) over all levels
     int* queue;         // device work-queue counter, zero before launch
+    const double* dt;   // device slot holding the time step
+    DiagSink diag;      // fused diagnostics of the new state, or all null
     T gamma;
     T gm1;              // gamma - 1, formed once on the host in FP64
 };
@@ -187,6 +197,19 @@ __device__ __forceinline__ void build_tables(const LevelArgs<T>& L, int g, int* 
     } else if (t == 0) {
         s_par[0] = -1;
     }
+}
+
+// FP32 signal speed c_s + max(|vx|,|vy|,|vz|) (denominator of Eq. CFL) and
+// pressure (Eqs. ThermalEnergy, EOS), written with explicitly rounded
+// intrinsics so that every translation unit evaluates it identically
+// whatever its contraction and precision flags.
+__device__ __forceinline__ void speed_pressure_f32(const float u[NV], float g, float gm1, float& s,
+                                                   float& P) {
+    const float ri = __fdividef(1.0f, u[0]);
+    const float m2 = fmaf(u[1], u[1], fmaf(u[2], u[2], __fmul_rn(u[3], u[3])));
+    P = __fmul_rn(gm1, fmaf(__fmul_rn(-0.5f, ri), m2, u[4]));
+    const float cs = __fsqrt_rn(__fmul_rn(__fmul_rn(g, fmaxf(P, 0.0f)), ri));
+    s = fmaf(fmaxf(fmaxf(fabsf(u[1]), fabsf(u[2])), fabsf(u[3])), ri, cs);
 }
 
 // Exact-order maximum of positive doubles through their bit patterns.

@@ -65,10 +65,18 @@ struct gamer_hydro_s {
     int sweep_threads = 512;
     int f64_chunk = 2048;
 
-    // graphs of advance_all, keyed by the launch arguments
+    // whole steps (gamer_hydro_step): captured CUDA graphs keyed by the
+    // launch arguments, replayed on the handle's stream
     std::map<std::string, GraphEntry> graphs;
     uint64_t use_clock = 0;
-    double* d_dt = nullptr;       // device copy of dt read by graph replays
+    cudaStream_t cap_stream = nullptr;
+    double* d_dt = nullptr;       // device time step read by every kernel
+    bool dt_ready = false;        // d_dt holds the step dt of the current state
+    uint64_t dt_version = 0;
+    StepOut* d_step = nullptr;    // device result of the last step
+    StepOut* h_step = nullptr;    // pinned host copy, written by the graph
+    cudaEvent_t step_event = nullptr;
+    cudaEvent_t prof_ev[2] = {nullptr, nullptr};   // recorded around the sweep launch
 };
 
 namespace {
@@ -117,8 +125,7 @@ int resolve_patch(const std::vector<int>& nbr, int g, int q[3]) {
 }
 
 template <typename T>
-void fill_level(LevelArgs<T>& a, const gamer_level_t* L, int l, const gamer_hydro_s* h,
-                double dt) {
+void fill_level(LevelArgs<T>& a, const gamer_level_t* L, int l, const gamer_hydro_s* h) {
     const gamer_level_t& c = L[l];
     a.u = static_cast<const T*>(c.u);
     a.u_out = static_cast<T*>(c.u_out);
@@ -132,7 +139,7 @@ void fill_level(LevelArgs<T>& a, const gamer_level_t* L, int l, const gamer_hydr
     a.n_groups_c = l > 0 ? L[l - 1].n_groups : 0;
     a.item0 = 0;
     a.pad_ = 0;
-    a.lam = (T)(dt / c.dh);
+    a.dh = c.dh;
 }
 
 size_t elem_size(const gamer_hydro_s* h) { return h->precision == GAMER_FP64 ? 8 : 4; }
@@ -298,6 +305,18 @@ int prepare(gamer_hydro_t h, const gamer_hierarchy_t* H) {
     h->total_groups = total;
     h->version = H->version;
     h->have_version = true;
+    if (h->precision == GAMER_FP64) {
+        // staging blocks of the plain FP64 path, allocated here so that no
+        // allocation happens while a step is being captured
+        int need = 0;
+        for (int l = 0; l < n; ++l) need = std::max(need, std::min(h->f64_chunk, H->levels[l].n_groups));
+        if (h->stage_groups < need) {
+            cudaFree(h->d_stage);
+            h->d_stage = nullptr;
+            CK(h, cudaMalloc(&h->d_stage, stage_f64_bytes_per_group() * need));
+            h->stage_groups = need;
+        }
+    }
     return ensure_diag(h, total);
 }
 
@@ -321,16 +340,19 @@ int check_level_arg(gamer_hydro_t h, const gamer_hierarchy_t* H, int level) {
     return GAMER_OK;
 }
 
-int advance_level_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, int l, double dt, int order) {
+// Sweep set of level l reading dt from h->d_dt; `diag` fuses the
+// diagnostics of the new state into the FP32 launch (single level only).
+int advance_level_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, int l, int order) {
     const gamer_level_t* L = H->levels;
     if (L[l].n_groups == 0) return GAMER_OK;
     if (h->precision == GAMER_FP32) {
         SweepArgs<float> a;
         memset(&a, 0, sizeof(a));
-        fill_level<float>(a.lv[0], L, l, h, dt);
+        fill_level<float>(a.lv[0], L, l, h);
         a.n_levels = 1;
         a.total = L[l].n_groups;
         a.queue = h->d_queue;
+        a.dt = h->d_dt;
         a.gamma = (float)h->gamma;
         a.gm1 = (float)(h->gamma - 1.0);
         CK(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), h->stream));
@@ -339,7 +361,7 @@ int advance_level_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, int l, doubl
     } else {
         LevelArgs<double> a;
         memset(&a, 0, sizeof(a));
-        fill_level<double>(a, L, l, h, dt);
+        fill_level<double>(a, L, l, h);
         const int chunk = std::min(h->f64_chunk, L[l].n_groups);
         if (h->stage_groups < chunk) {
             cudaFree(h->d_stage);
@@ -349,14 +371,14 @@ int advance_level_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, int l, doubl
         }
         for (int g0 = 0; g0 < L[l].n_groups; g0 += chunk) {
             const int cnt = std::min(chunk, L[l].n_groups - g0);
-            CK(h, launch_pg_f64(a, g0, cnt, order, h->limiter, h->gamma, h->gamma - 1.0, h->d_stage,
-                                h->stream));
+            CK(h, launch_pg_f64(a, g0, cnt, order, h->limiter, h->gamma, h->gamma - 1.0, h->d_dt,
+                                h->d_stage, h->stream));
         }
     }
     return GAMER_OK;
 }
 
-int fixup_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, int l, double dt) {
+int fixup_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, int l) {
     const gamer_level_t* L = H->levels;
     const LevelCache& c = h->lv[l];
     if (c.fix_list.empty()) return GAMER_OK;
@@ -365,20 +387,19 @@ int fixup_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, int l, double dt) {
     if (h->precision == GAMER_FP32) {
         FixArgs<float> a{c.d_fix_list, (float*)L[l].u_out, (const float*)L[l + 1].u_out, L[l].nbr,
                          L[l].child, (const float*)fc, (const float*)ff, L[l].n_groups,
-                         L[l + 1].n_groups, (float)(dt / L[l].dh)};
+                         L[l + 1].n_groups, h->d_dt, L[l].dh};
         CK(h, launch_fixup<float>(a, (int)c.fix_list.size(), h->stream));
     } else {
         FixArgs<double> a{c.d_fix_list, (double*)L[l].u_out, (const double*)L[l + 1].u_out, L[l].nbr,
                           L[l].child, (const double*)fc, (const double*)ff, L[l].n_groups,
-                          L[l + 1].n_groups, dt / L[l].dh};
+                          L[l + 1].n_groups, h->d_dt, L[l].dh};
         CK(h, launch_fixup<double>(a, (int)c.fix_list.size(), h->stream));
     }
     return GAMER_OK;
 }
 
 template <typename T>
-int diag_launch(gamer_hydro_t h, const gamer_hierarchy_t* H) {
-    DiagArgs<T> a;
+void diag_args(gamer_hydro_t h, const gamer_hierarchy_t* H, DiagArgs<T>& a) {
     memset(&a, 0, sizeof(a));
     int item = 0;
     for (int l = 0; l < H->n_levels; ++l) {
@@ -395,7 +416,13 @@ int diag_launch(gamer_hydro_t h, const gamer_hierarchy_t* H) {
     a.pg_sum = h->d_pg_sum;
     a.pg_bad = h->d_pg_bad;
     a.out = h->d_out;
-    CK(h, launch_diag<T>(a, item, h->stream));
+}
+
+template <typename T>
+int diag_launch(gamer_hydro_t h, const gamer_hierarchy_t* H) {
+    DiagArgs<T> a;
+    diag_args<T>(h, H, a);
+    CK(h, launch_diag<T>(a, h->total_groups, h->stream));
     return GAMER_OK;
 }
 
@@ -436,6 +463,108 @@ int diagnose_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, double cfl, doubl
     return GAMER_OK;
 }
 
+int check_same_parity(gamer_hydro_t h, const gamer_hierarchy_t* H) {
+    for (int l = 1; l < H->n_levels; ++l)
+        if (h->parity[l] != h->parity[0])
+            return fail(h, GAMER_ERR_STATE, "a whole step needs every level at the same sweep parity");
+    return GAMER_OK;
+}
+
+// Launch sequence of one whole step on stream st (dt read from h->d_dt):
+// every level's sweep set (the FP32 handle: one persistent launch over the
+// groups of all levels), the fix-ups from the finest level down, and, when
+// `with_diag`, the diagnostics of the new state and the step result (new
+// dt from Eq. CFL, held if the next step is a zyx step) with its copy to
+// pinned host memory.  Single-level FP32 steps fuse the per-group
+// diagnostics into the sweep launch.
+int enqueue_step(gamer_hydro_t h, const gamer_hierarchy_t* H, cudaStream_t st, bool with_diag, double cfl) {
+    const int n = H->n_levels;
+    const int order = h->parity[0];
+    cudaStream_t saved = h->stream;
+    h->stream = st;
+    int r = GAMER_OK;
+    const bool fused = with_diag && h->precision == GAMER_FP32 && n == 1;
+    DiagArgs<float> d32;
+    DiagArgs<double> d64;
+    if (h->precision == GAMER_FP32) {
+        SweepArgs<float> a;
+        memset(&a, 0, sizeof(a));
+        int item = 0;
+        for (int l = 0; l < n; ++l) {
+            fill_level<float>(a.lv[l], H->levels, l, h);
+            a.lv[l].item0 = item;
+            item += H->levels[l].n_groups;
+        }
+        a.n_levels = n;
+        a.total = item;
+        a.queue = h->d_queue;
+        a.dt = h->d_dt;
+        a.gamma = (float)h->gamma;
+        a.gm1 = (float)(h->gamma - 1.0);
+        if (fused) a.diag = DiagSink{h->d_pg_max, h->d_pg_sum, h->d_pg_bad};
+        if (item > 0) {
+            cudaError_t e = cudaMemsetAsync(h->d_queue, 0, sizeof(int), st);
+            if (e == cudaSuccess && h->prof_ev[0]) e = cudaEventRecord(h->prof_ev[0], st);
+            if (e == cudaSuccess) e = launch_sweep_f32(a, order, h->limiter, h->sweep_threads, std::min(item, h->sm_count), st);
+            if (e == cudaSuccess && h->prof_ev[1]) e = cudaEventRecord(h->prof_ev[1], st);
+            if (e != cudaSuccess) r = cuda_fail(h, e, "FP32 sweep launch");
+        }
+    } else {
+        if (h->prof_ev[0]) {
+            cudaError_t e = cudaEventRecord(h->prof_ev[0], st);
+            if (e != cudaSuccess) r = cuda_fail(h, e, "cudaEventRecord");
+        }
+        for (int l = 0; l < n && !r; ++l) r = advance_level_impl(h, H, l, order);
+        if (!r && h->prof_ev[1]) {
+            cudaError_t e = cudaEventRecord(h->prof_ev[1], st);
+            if (e != cudaSuccess) r = cuda_fail(h, e, "cudaEventRecord");
+        }
+    }
+    for (int l = n - 2; l >= 0 && !r; --l) r = fixup_impl(h, H, l);
+    if (!r && with_diag) {
+        // the diagnostics read the new state: u_out of every level
+        gamer_level_t lv[MAXLEV];
+        for (int l = 0; l < n; ++l) {
+            lv[l] = H->levels[l];
+            lv[l].u = H->levels[l].u_out;
+        }
+        gamer_hierarchy_t Hn = *H;
+        Hn.levels = lv;
+        double dh[MAXLEV];
+        for (int l = 0; l < n; ++l) dh[l] = H->levels[l].dh;
+        diag_args<float>(h, &Hn, d32);
+        diag_args<double>(h, &Hn, d64);
+        cudaError_t e = cudaSuccess;
+        if (!fused)
+            e = h->precision == GAMER_FP32 ? launch_diag_groups<float>(d32, h->total_groups, st)
+                                           : launch_diag_groups<double>(d64, h->total_groups, st);
+        // the step after this one is an xyz step exactly when this one is zyx
+        if (e == cudaSuccess)
+            e = launch_step_final(d32, d64, h->precision == GAMER_FP64, dh, cfl, h->d_dt, order == 1,
+                                  h->d_step, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->h_step, h->d_step, sizeof(StepOut), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) r = cuda_fail(h, e, "step diagnostics");
+    }
+    h->stream = saved;
+    return r;
+}
+
+// dt of the current state (Eq. CFL) into h->d_dt, on the handle's stream.
+int diagnose_to_device(gamer_hydro_t h, const gamer_hierarchy_t* H, double cfl) {
+    DiagArgs<float> d32;
+    DiagArgs<double> d64;
+    diag_args<float>(h, H, d32);
+    diag_args<double>(h, H, d64);
+    double dh[MAXLEV];
+    for (int l = 0; l < H->n_levels; ++l) dh[l] = H->levels[l].dh;
+    cudaError_t e = h->precision == GAMER_FP32 ? launch_diag_groups<float>(d32, h->total_groups, h->stream)
+                                               : launch_diag_groups<double>(d64, h->total_groups, h->stream);
+    if (e == cudaSuccess) e = launch_step_final(d32, d64, h->precision == GAMER_FP64, dh, cfl, h->d_dt, 1, h->d_step, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "initial CFL time step");
+    return GAMER_OK;
+}
+
 }  // namespace
 
 // =================================================================== C ABI
@@ -460,10 +589,19 @@ int gamer_hydro_create(double gamma, int limiter, int ghost_width, int precision
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_queue, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_dt, sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_step, sizeof(StepOut));
+    if (e == cudaSuccess) e = cudaMemset(h->d_step, 0, sizeof(StepOut));
+    if (e == cudaSuccess) e = cudaMallocHost(&h->h_step, sizeof(StepOut));
+    if (e == cudaSuccess) memset(h->h_step, 0, sizeof(StepOut));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->step_event, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = sweep_f32_init();
     if (e != cudaSuccess) {
         std::string m = std::string("CUDA initialisation failed: ") + cudaGetErrorString(e);
         cudaFree(h->d_queue);
         cudaFree(h->d_dt);
+        cudaFree(h->d_step);
+        cudaFreeHost(h->h_step);
+        if (h->step_event) cudaEventDestroy(h->step_event);
         delete h;
         return fail(nullptr, GAMER_ERR_CUDA, m);
     }
@@ -485,6 +623,10 @@ int gamer_hydro_destroy(gamer_hydro_t h) {
     cudaFree(h->d_out);
     cudaFreeHost(h->h_out);
     cudaFree(h->d_stage);
+    cudaFree(h->d_step);
+    cudaFreeHost(h->h_step);
+    if (h->step_event) cudaEventDestroy(h->step_event);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
     return GAMER_OK;
 }
@@ -542,7 +684,9 @@ int gamer_hydro_advance(gamer_hydro_t h, const gamer_hierarchy_t* H, int level, 
     if (r) return r;
     if ((r = check_level_arg(h, H, level))) return r;
     if ((r = check_pointers(h, H, true))) return r;
-    r = advance_level_impl(h, H, level, dt, h->parity[level]);
+    CK(h, launch_set_dt(h->d_dt, dt, h->stream));
+    h->dt_ready = false;
+    r = advance_level_impl(h, H, level, h->parity[level]);
     if (r) return r;
     h->parity[level] ^= 1;
     return GAMER_OK;
@@ -557,7 +701,9 @@ int gamer_hydro_fixup(gamer_hydro_t h, const gamer_hierarchy_t* H, int level, do
     if ((r = check_pointers(h, H, true))) return r;
     if (level < 0 || level + 1 >= H->n_levels)
         return fail(h, GAMER_ERR_ARG, "fixup level must be in [0, n_levels-2]");
-    return fixup_impl(h, H, level, dt);
+    CK(h, launch_set_dt(h->d_dt, dt, h->stream));
+    h->dt_ready = false;
+    return fixup_impl(h, H, level);
 }
 
 int gamer_hydro_advance_all(gamer_hydro_t h, const gamer_hierarchy_t* H, double dt) {
@@ -567,37 +713,93 @@ int gamer_hydro_advance_all(gamer_hydro_t h, const gamer_hierarchy_t* H, double 
     int r = prepare(h, H);
     if (r) return r;
     if ((r = check_pointers(h, H, true))) return r;
-    const int n = H->n_levels;
-    const int order = h->parity[0];
-    for (int l = 1; l < n; ++l)
-        if (h->parity[l] != order)
-            return fail(h, GAMER_ERR_STATE, "advance_all needs every level at the same sweep parity");
-    if (h->precision == GAMER_FP32) {
-        SweepArgs<float> a;
-        memset(&a, 0, sizeof(a));
-        int item = 0;
-        for (int l = 0; l < n; ++l) {
-            fill_level<float>(a.lv[l], H->levels, l, h, dt);
-            a.lv[l].item0 = item;
-            item += H->levels[l].n_groups;
-        }
-        a.n_levels = n;
-        a.total = item;
-        a.queue = h->d_queue;
-        a.gamma = (float)h->gamma;
-        a.gm1 = (float)(h->gamma - 1.0);
-        if (item > 0) {
-            CK(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), h->stream));
-            const int grid = std::min(item, h->sm_count);
-            CK(h, launch_sweep_f32(a, order, h->limiter, h->sweep_threads, grid, h->stream));
-        }
-    } else {
-        for (int l = 0; l < n; ++l)
-            if ((r = advance_level_impl(h, H, l, dt, order))) return r;
+    if ((r = check_same_parity(h, H))) return r;
+    CK(h, launch_set_dt(h->d_dt, dt, h->stream));
+    h->dt_ready = false;
+    if ((r = enqueue_step(h, H, h->stream, false, 0.0))) return r;
+    for (int l = 0; l < H->n_levels; ++l) h->parity[l] ^= 1;
+    return GAMER_OK;
+}
+
+int gamer_hydro_step(gamer_hydro_t h, const gamer_hierarchy_t* H, double cfl) {
+    if (!h) return GAMER_ERR_ARG;
+    if (!(cfl > 0.0) || !std::isfinite(cfl)) return fail(h, GAMER_ERR_ARG, "cfl must be positive");
+    CK(h, cudaSetDevice(h->device));
+    int r = prepare(h, H);
+    if (r) return r;
+    if ((r = check_pointers(h, H, true))) return r;
+    if ((r = check_same_parity(h, H))) return r;
+    if (!h->dt_ready || h->dt_version != h->version) {
+        // first step on this state: dt from Eq. CFL of the current state
+        if ((r = diagnose_to_device(h, H, cfl))) return r;
+        h->dt_ready = true;
+        h->dt_version = h->version;
     }
-    for (int l = n - 2; l >= 0; --l)
-        if ((r = fixup_impl(h, H, l, dt))) return r;
-    for (int l = 0; l < n; ++l) h->parity[l] ^= 1;
+    if (h->prof_ev[0]) {
+        // profiled steps launch directly: events recorded inside a graph
+        // cannot be timed
+        if ((r = enqueue_step(h, H, h->stream, true, cfl))) return r;
+        CK(h, cudaEventRecord(h->step_event, h->stream));
+        for (int l = 0; l < H->n_levels; ++l) h->parity[l] ^= 1;
+        return GAMER_OK;
+    }
+    // graph of the whole step, keyed by everything the kernels are given
+    char key[64];
+    std::string k;
+    snprintf(key, sizeof(key), "%llu|%d|%.17g|", (unsigned long long)h->version, h->parity[0], cfl);
+    k = key;
+    for (int l = 0; l < H->n_levels; ++l) {
+        snprintf(key, sizeof(key), "%p,%p,%p;", H->levels[l].u, H->levels[l].u_out, H->levels[l].face_flux);
+        k += key;
+    }
+    auto it = h->graphs.find(k);
+    if (it == h->graphs.end()) {
+        if (!h->cap_stream) CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        if (h->graphs.size() >= 16) drop_graphs(h);
+        cudaGraph_t graph = nullptr;
+        CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        r = enqueue_step(h, H, h->cap_stream, true, cfl);
+        cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (r) {
+            if (graph) cudaGraphDestroy(graph);
+            return r;
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+        GraphEntry ge;
+        e = cudaGraphInstantiate(&ge.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+        it = h->graphs.emplace(k, ge).first;
+    }
+    it->second.last_use = ++h->use_clock;
+    CK(h, cudaGraphLaunch(it->second.exec, h->stream));
+    CK(h, cudaEventRecord(h->step_event, h->stream));
+    for (int l = 0; l < H->n_levels; ++l) h->parity[l] ^= 1;
+    return GAMER_OK;
+}
+
+int gamer_hydro_step_result(gamer_hydro_t h, double* dt_used, double* dt_next, double sums[5],
+                            int64_t* n_bad) {
+    if (!h) return GAMER_ERR_ARG;
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaEventSynchronize(h->step_event));
+    const StepOut& o = *h->h_step;
+    if (o.steps == 0) return fail(h, GAMER_ERR_STATE, "no step has completed on this handle");
+    if (dt_used) *dt_used = o.dt_used;
+    if (dt_next) *dt_next = o.dt_next;
+    if (sums)
+        for (int v = 0; v < NV; ++v) sums[v] = o.sum[v];
+    if (n_bad) *n_bad = o.n_bad;
+    return GAMER_OK;
+}
+
+int gamer_hydro_set_profiling(gamer_hydro_t h, void* ev_before, void* ev_after) {
+    if (!h) return GAMER_ERR_ARG;
+    if ((ev_before == nullptr) != (ev_after == nullptr))
+        return fail(h, GAMER_ERR_ARG, "give both events or neither");
+    h->prof_ev[0] = static_cast<cudaEvent_t>(ev_before);
+    h->prof_ev[1] = static_cast<cudaEvent_t>(ev_after);
+    drop_graphs(h);
     return GAMER_OK;
 }
 

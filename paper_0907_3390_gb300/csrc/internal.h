@@ -13,8 +13,9 @@ namespace gh {
 cudaError_t launch_sweep_f32(const SweepArgs<float>& a, int order, int lim, int threads, int grid,
                              cudaStream_t st);
 size_t sweep_f32_smem();
+cudaError_t sweep_f32_init();
 cudaError_t launch_pg_f64(const LevelArgs<double>& L, int g0, int count, int order, int lim,
-                          double gamma, double gm1, double* stage, cudaStream_t st);
+                          double gamma, double gm1, const double* dt, double* stage, cudaStream_t st);
 size_t stage_f64_bytes_per_group();
 
 // ---- fix-up: coarse level c corrected from fine level c+1
@@ -28,7 +29,8 @@ struct FixArgs {
     const T* flux_c;      // coarse face fluxes
     const T* flux_f;      // fine face fluxes
     int n_c, n_f;         // groups on the two levels
-    T lam;                // dt / dh of the coarse level
+    const double* dt;     // device slot holding the time step
+    double dh;            // coarse cell width
 };
 template <typename T>
 cudaError_t launch_fixup(const FixArgs<T>& a, int n_list, cudaStream_t st);
@@ -58,5 +60,24 @@ struct DiagArgs {
 };
 template <typename T>
 cudaError_t launch_diag(const DiagArgs<T>& a, int total, cudaStream_t st);
+// per-group diagnostics only (no per-level reduction)
+template <typename T>
+cudaError_t launch_diag_groups(const DiagArgs<T>& a, int total, cudaStream_t st);
+
+// Result of one whole step, written on the device.
+struct StepOut {
+    double dt_used;     // dt of the step just taken
+    double dt_next;     // dt the next step will use (held for a zyx step)
+    double dt_cfl;      // Eq. CFL from the new state
+    double sum[NV];     // leaf sums of u * dh^3
+    long long n_bad;
+    long long steps;
+};
+// One block: per-level reduction of the per-group diagnostics in fixed
+// order, then dt from Eq. CFL (written to *dt when update_dt != 0).
+cudaError_t launch_step_final(const DiagArgs<float>& a32, const DiagArgs<double>& a64, bool fp64,
+                              const double* dh, double cfl, double* dt, int update_dt,
+                              StepOut* out, cudaStream_t st);
+cudaError_t launch_set_dt(double* slot, double dt, cudaStream_t st);
 
 }  // namespace gh

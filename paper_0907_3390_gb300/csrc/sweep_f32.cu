@@ -36,7 +36,7 @@ namespace gh {
 
 constexpr int XP = 23;                    // x pitch: odd, so x-sweep columns hit distinct banks
 constexpr int VS = PD * PD * XP;          // floats per variable in shared memory
-constexpr size_t SMEM_F32 = (size_t)NV * VS * sizeof(float) + 256 * sizeof(int);   // block + 2 item tables
+constexpr size_t SMEM_F32 = (size_t)NV * VS * sizeof(float) + 512 * sizeof(int);   // block + item tables + reduction
 
 // A = c u + F (= 2 F^R) and B = c u - F (= 2 F^L) of one cell for a sweep
 // along AXIS (Eq. LRFlux with w = F/c substituted): c = |v_n| + c_s
@@ -231,6 +231,7 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
 struct ItemTab {
     int src[27], mask[27], csrc[27], cmask[27];
     int item, level, g, par;
+    float lam;          // dt / dh, formed in FP64 from the device time step
 };
 
 __device__ __forceinline__ int level_of(const SweepArgs<float>& a, int item) {
@@ -253,6 +254,7 @@ __device__ __forceinline__ void build_tab(ItemTab& t, const SweepArgs<float>& a,
         t.level = l;
         t.g = g;
         t.par = L.parent != nullptr ? L.parent[g] : -1;
+        t.lam = (float)(*a.dt / L.dh);
     }
 }
 
@@ -393,21 +395,100 @@ __device__ __forceinline__ void gather_set(float* sm, const SweepArgs<float>& a,
     }
 }
 
-// Interior 16^3 -> u_out: one item per (variable, interior x-row), two
-// aligned 16-byte stores per patch row.
+// Double-float (hi, lo) accumulation, error-free in each step (two-sum).
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
+    const float s = hi + x;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (x - bb);
+    hi = s;
+}
+
+// Interior 16^3 -> u_out, one interior x-row (16 cells) per thread, two
+// aligned 16-byte stores per patch row and variable.  With diagnostics on,
+// the thread also accumulates the exact speed maximum (as the bit pattern
+// of a non-negative float, so a NaN wins), double-float sums of the five
+// variables and the count of bad cells; warps reduce with shuffles and
+// lane 0 parks the warp's result in red[warp][12].
 __device__ __forceinline__ void store_rows(const float* sm, const LevelArgs<float>& L, int g, int t0,
-                                           int stride) {
+                                           int stride, bool diag, float gam, float gm1, float* red) {
     const size_t vstride = (size_t)L.n_groups * 8 * 512;
-    for (int it = t0; it < NV * GS * GS; it += stride) {
-        const int v = it / (GS * GS), r = it % (GS * GS);
+    unsigned smax = 0u;
+    float hi[NV] = {0.f, 0.f, 0.f, 0.f, 0.f}, lo[NV] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    int bad = 0;
+    for (int r = t0; r < GS * GS; r += stride) {
         const int y = r % GS, z = r / GS;
-        const float* s = sm + v * VS + ((z + NG) * PD + (y + NG)) * XP + NG;
-        float* o = L.u_out + v * vstride + cell_offset(g, 0, y, z);
+        const float* s = sm + ((z + NG) * PD + (y + NG)) * XP + NG;
+        float* o = L.u_out + cell_offset(g, 0, y, z);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const float4 q = make_float4(s[4 * j], s[4 * j + 1], s[4 * j + 2], s[4 * j + 3]);
-            *reinterpret_cast<float4*>(o + (j >> 1) * 512 + (j & 1) * 4) = q;
+            float u[4][NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) u[q][v] = s[v * VS + 4 * j + q];
+                *reinterpret_cast<float4*>(o + v * vstride + (j >> 1) * 512 + (j & 1) * 4) =
+                    make_float4(u[0][v], u[1][v], u[2][v], u[3][v]);
+            }
+            if (diag) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float sp, P;
+                    speed_pressure_f32(u[q], gam, gm1, sp, P);
+                    smax = max(smax, __float_as_uint(sp));
+                    bool fin = true;
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        df_add(hi[v], lo[v], u[q][v]);
+                        fin = fin && isfinite(u[q][v]);
+                    }
+                    bad += (!fin || !(u[q][0] > 0.0f) || !(P > 0.0f)) ? 1 : 0;
+                }
+            }
         }
+    }
+    if (!diag) return;
+    const unsigned full = 0xffffffffu;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const float oh = __shfl_xor_sync(full, hi[v], w), ol = __shfl_xor_sync(full, lo[v], w);
+            df_add(hi[v], lo[v], oh);
+            lo[v] += ol;
+        }
+    }
+    smax = __reduce_max_sync(full, smax);
+    bad = __reduce_add_sync(full, bad);
+    if ((threadIdx.x & 31) == 0) {
+        float* rr = red + (threadIdx.x >> 5) * 12;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            rr[2 * v] = hi[v];
+            rr[2 * v + 1] = lo[v];
+        }
+        rr[10] = __uint_as_float(smax);
+        rr[11] = __int_as_float(bad);
+    }
+}
+
+// Combine the parked warp results of one item (threads 0..5) and write the
+// item's diagnostics: per-variable FP64 sums, the speed maximum as the bit
+// pattern of a double, the bad-cell count.
+__device__ __forceinline__ void finish_diag(const DiagSink& d, int item, const float* red, int nwarps) {
+    const int t = threadIdx.x;
+    if (t < NV) {
+        double s = 0.0;
+        for (int w = 0; w < nwarps; ++w) s += (double)red[w * 12 + 2 * t] + (double)red[w * 12 + 2 * t + 1];
+        d.pg_sum[(size_t)item * NV + t] = s;
+    } else if (t == NV) {
+        unsigned m = 0u;
+        int b = 0;
+        for (int w = 0; w < nwarps; ++w) {
+            m = max(m, __float_as_uint(red[w * 12 + 10]));
+            b += __float_as_int(red[w * 12 + 11]);
+        }
+        d.pg_max[item] = (unsigned long long)__double_as_longlong((double)__uint_as_float(m));
+        d.pg_bad[item] = b;
     }
 }
 
@@ -427,7 +508,9 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> 
     extern __shared__ float sm[];
     ItemTab* tab = reinterpret_cast<ItemTab*>(sm + NV * VS);     // [2]
     int* s_item = reinterpret_cast<int*>(tab + 2);               // current, next
+    float* s_red = reinterpret_cast<float*>(s_item + 2);         // [8 warps][12]
     const int tid = threadIdx.x;
+    const bool diag = args.diag.pg_max != nullptr;
 
     if (tid == 0) {
         s_item[0] = atomicAdd(args.queue, 1);
@@ -460,21 +543,25 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> 
         const LevelArgs<float>& L = args.lv[cur.level];
         float* fg = L.flux ? L.flux + (size_t)cur.g * FLUX_PG : nullptr;
 
-        sweep<ORDER, 0, LIM>(sm, L.lam, args.gamma, args.gm1, fg, NT_F32);
+        const float lam = cur.lam;
+        const int cur_item = cur.item;
+
+        sweep<ORDER, 0, LIM>(sm, lam, args.gamma, args.gm1, fg, NT_F32);
         __syncthreads();
-        if (tid < 11 * 32) sweep<ORDER, 1, LIM>(sm, L.lam, args.gamma, args.gm1, fg, 11 * 32);
+        if (tid < 11 * 32) sweep<ORDER, 1, LIM>(sm, lam, args.gamma, args.gm1, fg, 11 * 32);
         else if (has_next) gather_set<ORDER, 0>(sm, args, nxt, tid - 11 * 32, NT_F32 - 11 * 32);
         __syncthreads();
-        if (tid < 8 * 32) sweep<ORDER, 2, LIM>(sm, L.lam, args.gamma, args.gm1, fg, 8 * 32);
+        if (tid < 8 * 32) sweep<ORDER, 2, LIM>(sm, lam, args.gamma, args.gm1, fg, 8 * 32);
         else if (has_next) gather_set<ORDER, 1>(sm, args, nxt, tid - 8 * 32, NT_F32 - 8 * 32);
         __syncthreads();
-        if (tid < 8 * 32) store_rows(sm, L, cur.g, tid, 8 * 32);
+        if (tid < 8 * 32) store_rows(sm, L, cur.g, tid, 8 * 32, diag, args.gamma, args.gm1, s_red);
         else if (has_next) gather_set<ORDER, 2>(sm, args, nxt, tid - 8 * 32, NT_F32 - 8 * 32);
         if (tid == 0) {
             s_item[0] = next;
             s_item[1] = has_next ? atomicAdd(args.queue, 1) : next;
         }
         __syncthreads();
+        if (diag) finish_diag(args.diag, cur_item, s_red, 8);
         if (!has_next) break;
         slot ^= 1;
         gather_set<ORDER, 3>(sm, args, tab[slot], tid, NT_F32);
@@ -482,11 +569,25 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> 
 }
 
 template <int ORDER, int LIM>
+static cudaError_t set_smem_attr() {
+    return cudaFuncSetAttribute(k_sweep_f32<ORDER, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)SMEM_F32);
+}
+
+// Opt every instantiation into the large dynamic shared memory once per
+// process and device (not a stream operation, so it stays out of graph
+// capture).
+cudaError_t sweep_f32_init() {
+    cudaError_t e = set_smem_attr<0, 0>();
+    if (e == cudaSuccess) e = set_smem_attr<0, 1>();
+    if (e == cudaSuccess) e = set_smem_attr<1, 0>();
+    if (e == cudaSuccess) e = set_smem_attr<1, 1>();
+    return e;
+}
+
+template <int ORDER, int LIM>
 static cudaError_t launch_one(const SweepArgs<float>& a, int grid, cudaStream_t st) {
-    auto k = k_sweep_f32<ORDER, LIM>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_F32);
-    if (e != cudaSuccess) return e;
-    k<<<grid, NT_F32, SMEM_F32, st>>>(a);
+    k_sweep_f32<ORDER, LIM><<<grid, NT_F32, SMEM_F32, st>>>(a);
     return cudaGetLastError();
 }
 

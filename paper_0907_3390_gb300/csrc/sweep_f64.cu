@@ -171,8 +171,11 @@ constexpr int NT64 = 256;
 // Group g0 + blockIdx.x of level L; scratch block blockIdx.x of `stage`.
 template <int ORDER, int LIM>
 __global__ void __launch_bounds__(NT64) k_pg_f64(const LevelArgs<double> L, int g0, double gamma,
-                                                  double gm1, double* __restrict__ stage) {
+                                                  double gm1, const double* __restrict__ dt,
+                                                  double* __restrict__ stage) {
     __shared__ int s_tab[160];
+    __shared__ double s_lam;
+    if (threadIdx.x == 0) s_lam = *dt / L.dh;   // lambda = dt / dh (Eq. FullstepValue)
     int* s_src = s_tab;
     int* s_mask = s_tab + 32;
     int* s_csrc = s_tab + 64;
@@ -191,11 +194,11 @@ __global__ void __launch_bounds__(NT64) k_pg_f64(const LevelArgs<double> L, int 
     gather_block<double, XP64, NT64>(blk, VS64, L, g, s_src, s_mask, s_csrc, s_cmask, ppx, ppy, ppz);
     __syncthreads();
     double* fg = L.flux ? L.flux + (size_t)g * FLUX_PG : nullptr;
-    sweep64<NT64, ORDER, 0, LIM>(blk, L.lam, gamma, gm1, fg);
+    sweep64<NT64, ORDER, 0, LIM>(blk, s_lam, gamma, gm1, fg);
     __syncthreads();
-    sweep64<NT64, ORDER, 1, LIM>(blk, L.lam, gamma, gm1, fg);
+    sweep64<NT64, ORDER, 1, LIM>(blk, s_lam, gamma, gm1, fg);
     __syncthreads();
-    sweep64<NT64, ORDER, 2, LIM>(blk, L.lam, gamma, gm1, fg);
+    sweep64<NT64, ORDER, 2, LIM>(blk, s_lam, gamma, gm1, fg);
     __syncthreads();
     const size_t vstride = (size_t)L.n_groups * 8 * 512;
     double* out = L.u_out + ((size_t)g << 12);
@@ -213,14 +216,14 @@ __global__ void __launch_bounds__(NT64) k_pg_f64(const LevelArgs<double> L, int 
 size_t stage_f64_bytes_per_group() { return BLK64 * sizeof(double); }
 
 cudaError_t launch_pg_f64(const LevelArgs<double>& L, int g0, int count, int order, int lim,
-                          double gamma, double gm1, double* stage, cudaStream_t st) {
+                          double gamma, double gm1, const double* dt, double* stage, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     if (order == 0) {
-        if (lim == 0) k_pg_f64<0, 0><<<count, NT64, 0, st>>>(L, g0, gamma, gm1, stage);
-        else k_pg_f64<0, 1><<<count, NT64, 0, st>>>(L, g0, gamma, gm1, stage);
+        if (lim == 0) k_pg_f64<0, 0><<<count, NT64, 0, st>>>(L, g0, gamma, gm1, dt, stage);
+        else k_pg_f64<0, 1><<<count, NT64, 0, st>>>(L, g0, gamma, gm1, dt, stage);
     } else {
-        if (lim == 0) k_pg_f64<1, 0><<<count, NT64, 0, st>>>(L, g0, gamma, gm1, stage);
-        else k_pg_f64<1, 1><<<count, NT64, 0, st>>>(L, g0, gamma, gm1, stage);
+        if (lim == 0) k_pg_f64<1, 0><<<count, NT64, 0, st>>>(L, g0, gamma, gm1, dt, stage);
+        else k_pg_f64<1, 1><<<count, NT64, 0, st>>>(L, g0, gamma, gm1, dt, stage);
     }
     return cudaGetLastError();
 }

@@ -357,3 +357,50 @@ def test_parity_state_and_resume():
     assert np.array_equal(D3.states()[0], resumed[0])
     for s in (S, S2, S3):
         s.close()
+
+
+# ------------------------------------------------------------ whole steps
+
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_step_api_matches_host_driven_steps(prec):
+    """gamer_hydro_step (device dt, fused diagnostics, CUDA graph) gives the
+    same states, dt sequence and sums as host-driven advance_all +
+    cfl_dt + check calls."""
+    u, npg = wl.smooth_grf(32, seed=5)
+    H, st = wl.single_level(u, npg)
+    S1 = B.Solver(G, 0, prec[0])
+    D1 = B.DeviceHierarchy(H, st, prec[1])
+    S2 = B.Solver(G, 0, prec[0])
+    D2 = B.DeviceHierarchy(H, st, prec[1])
+    dt = None
+    for c in range(6):
+        if c % 2 == 0:
+            dt = B.gamer_hydro_cfl_dt(S1.h, D1, 0.5)
+        B.gamer_hydro_advance_all(S1.h, D1, dt)
+        D1.swap()
+        B.gamer_hydro_step(S2.h, D2, 0.5)
+        D2.swap()
+        du, dn, sums, nb = B.gamer_hydro_step_result(S2.h)
+        assert du == dt
+        rs, rb = B.gamer_hydro_check(S1.h, D1)
+        assert nb == rb == 0
+        assert np.allclose(sums, rs, rtol=1e-13, atol=0)
+        assert np.array_equal(D1.states()[0], D2.states()[0])
+    S1.close()
+    S2.close()
+
+
+def test_step_api_amr_conserves():
+    H, st = amr_case()
+    for prec in (F64, F32):
+        S = B.Solver(G, 0, prec[0])
+        D = B.DeviceHierarchy(H, st, prec[1])
+        s0, _ = B.gamer_hydro_check(S.h, D)
+        for _ in range(4):
+            B.gamer_hydro_step(S.h, D, 0.5)
+            D.swap()
+        du, dn, s1, nb = B.gamer_hydro_step_result(S.h)
+        assert nb == 0
+        tol = 1e-12 if prec is F64 else 1e-6
+        assert np.all(np.abs(s1 - s0) / (np.abs(s0) + 1e-3) < tol), (s1 - s0)
+        S.close()
