@@ -184,6 +184,32 @@ int gamer_hydro_check(gamer_hydro_t h, const gamer_hierarchy_t *H, double sums[5
 int gamer_hydro_diagnose(gamer_hydro_t h, const gamer_hierarchy_t *H, double cfl,
                          double *dt_out, double sums[5], int64_t *n_bad);
 
+/* The CFL time step and the conservation / positivity check of
+ * gamer_hydro_diagnose, without a handle and without allocating any device
+ * memory.  The paper has no counterpart; this is for callers that cannot
+ * call cudaMalloc -- a thread that must not synchronise the device (as
+ * cudaMalloc/cudaFree may), code running inside a memory arena that owns
+ * all of the GPU's memory, a periodic health check that must not disturb
+ * the caller's allocator.
+ * The per-group scratch is one fixed array in the library's device memory
+ * (3.4 MB, held by every GPU that loads the library until the process
+ * exits) covering at most 65536 patch groups summed over levels; larger
+ * hierarchies get GAMER_ERR_ARG.  The caller passes the inputs (H: every
+ * level's u, n_groups, dh, and child below the finest level) and the host
+ * outputs (dt_out, sums, n_bad: any may be NULL); gamma and precision are
+ * those of the data.  Work runs on cuda_stream (NULL: legacy stream) and
+ * the call waits for it.  The first call on a device looks the scratch
+ * address up (cudaGetSymbolAddress) for that device, so make that first
+ * call before any stream capture.  All calls in the process share the
+ * scratch and each call rewrites every part it reads, so no state carries
+ * over; calls that overlap on the GPU (other threads, other streams) race
+ * on it and must be serialised by the caller.  Errors: GAMER_ERR_ARG,
+ * GAMER_ERR_CUDA, GAMER_ERR_UNSUPPORTED (device index above 63); the
+ * message is available from gamer_hydro_last_error(NULL) on this thread. */
+int gamer_hydro_diagnose_noalloc(double gamma, int precision, const gamer_hierarchy_t *H,
+                                 double cfl, void *cuda_stream, double *dt_out, double sums[5],
+                                 int64_t *n_bad);
+
 /* Profiling hook: CUDA events (cudaEvent_t, created with timing enabled)
  * that every later advance_all / step records immediately before and after
  * its sweep launches, so the caller can time the dominant kernel with
@@ -194,7 +220,8 @@ int gamer_hydro_diagnose(gamer_hydro_t h, const gamer_hierarchy_t *H, double cfl
 int gamer_hydro_set_profiling(gamer_hydro_t h, void *ev_before, void *ev_after);
 
 /* Message of the last failed call on this handle ("" if none).  With a NULL
- * handle, the message of the last failed gamer_hydro_create on this thread.
+ * handle, the message of the last failed handle-free call on this thread
+ * (gamer_hydro_create, gamer_hydro_diagnose_noalloc).
  * The string stays valid until the next call on the handle. */
 const char *gamer_hydro_last_error(gamer_hydro_t h);
 

@@ -26,7 +26,7 @@ EXPORTS = [
     "gamer_hydro_set_parity", "gamer_hydro_get_parity", "gamer_hydro_cfl_dt",
     "gamer_hydro_advance", "gamer_hydro_fixup", "gamer_hydro_advance_all",
     "gamer_hydro_check", "gamer_hydro_diagnose", "gamer_hydro_step", "gamer_hydro_step_result",
-    "gamer_hydro_set_profiling", "gamer_hydro_last_error",
+    "gamer_hydro_diagnose_noalloc", "gamer_hydro_set_profiling", "gamer_hydro_last_error",
 ]
 
 
@@ -80,6 +80,8 @@ def load(build_if_needed: bool = True) -> C.CDLL:
         L.gamer_hydro_diagnose.argtypes = [H, hp, C.c_double, dp, dp, C.POINTER(C.c_int64)]
         L.gamer_hydro_step.argtypes = [H, hp, C.c_double]
         L.gamer_hydro_step_result.argtypes = [H, dp, dp, dp, C.POINTER(C.c_int64)]
+        L.gamer_hydro_diagnose_noalloc.argtypes = [C.c_double, C.c_int, hp, C.c_double, vp, dp, dp,
+                                                   C.POINTER(C.c_int64)]
         L.gamer_hydro_set_profiling.argtypes = [H, vp, vp]
         L.gamer_hydro_last_error.argtypes = [H]
         L.gamer_hydro_last_error.restype = C.c_char_p
@@ -169,6 +171,18 @@ def gamer_hydro_step_result(h):
     nb = C.c_int64()
     _check(h, load().gamer_hydro_step_result(h, C.byref(du), C.byref(dn), sums, C.byref(nb)))
     return du.value, dn.value, np.array(sums[:]), int(nb.value)
+
+
+def gamer_hydro_diagnose_noalloc(gamma: float, precision: int, H, cfl: float, stream=None):
+    """(dt, sums[5], n_bad) without a handle or any device allocation."""
+    raw = None if stream is None else getattr(stream, "cuda_stream", stream)
+    dt = C.c_double()
+    sums = (C.c_double * 5)()
+    nb = C.c_int64()
+    _check(None, load().gamer_hydro_diagnose_noalloc(gamma, precision, H.struct(), cfl,
+                                                     C.c_void_p(raw) if raw else None, C.byref(dt), sums,
+                                                     C.byref(nb)))
+    return dt.value, np.array(sums[:]), int(nb.value)
 
 
 def gamer_hydro_set_profiling(h, ev_before, ev_after) -> None:

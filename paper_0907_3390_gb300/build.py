@@ -7,7 +7,8 @@ Each translation unit is compiled in parallel, then linked with
   (the FP32 path states its tolerance against the FP64 oracle);
 * sweep_f64.cu, aux_kernels.cu: ``-fmad=false`` so FP64 results round
   exactly as the plain definition of the scheme;
-* hydro_api.cu: host code of the C ABI.
+* hydro_api.cu: host code of the C ABI;
+* noalloc.cu: the allocation-free diagnostics entry point.
 """
 from __future__ import annotations
 
@@ -31,6 +32,7 @@ UNITS = {
     "sweep_f64.cu": ["-fmad=false"],
     "aux_kernels.cu": ["-fmad=false"],
     "hydro_api.cu": [],
+    "noalloc.cu": [],
 }
 
 

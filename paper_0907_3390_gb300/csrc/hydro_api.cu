@@ -18,6 +18,12 @@ namespace {
 
 thread_local std::string g_create_error;
 
+}  // namespace
+
+void gh::set_thread_error(const std::string& msg) { g_create_error = msg; }
+
+namespace {
+
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     uint64_t last_use = 0;

@@ -3,6 +3,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -79,5 +80,9 @@ cudaError_t launch_step_final(const DiagArgs<float>& a32, const DiagArgs<double>
                               const double* dh, double cfl, double* dt, int update_dt,
                               StepOut* out, cudaStream_t st);
 cudaError_t launch_set_dt(double* slot, double dt, cudaStream_t st);
+
+// Message of the last failed handle-free call on this thread (read back by
+// gamer_hydro_last_error(NULL)).
+void set_thread_error(const std::string& msg);
 
 }  // namespace gh
