@@ -208,7 +208,10 @@ __device__ __forceinline__ void speed_pressure_f32(const float u[NV], float g, f
     const float ri = __fdividef(1.0f, u[0]);
     const float m2 = fmaf(u[1], u[1], fmaf(u[2], u[2], __fmul_rn(u[3], u[3])));
     P = __fmul_rn(gm1, fmaf(__fmul_rn(-0.5f, ri), m2, u[4]));
-    const float cs = __fsqrt_rn(__fmul_rn(__fmul_rn(g, fmaxf(P, 0.0f)), ri));
+    const float x = __fmul_rn(__fmul_rn(g, fmaxf(P, 0.0f)), ri);
+    // sqrt(x) through the reciprocal square root; x = 0 gives 0, a negative
+    // or NaN x gives NaN (as sqrt would)
+    const float cs = x == 0.0f ? 0.0f : __fmul_rn(x, rsqrtf(x));
     s = fmaf(fmaxf(fmaxf(fabsf(u[1]), fabsf(u[2])), fabsf(u[3])), ri, cs);
 }
 

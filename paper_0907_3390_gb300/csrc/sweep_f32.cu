@@ -36,7 +36,7 @@ namespace gh {
 
 constexpr int XP = 23;                    // x pitch: odd, so x-sweep columns hit distinct banks
 constexpr int VS = PD * PD * XP;          // floats per variable in shared memory
-constexpr size_t SMEM_F32 = (size_t)NV * VS * sizeof(float) + 512 * sizeof(int);   // block + item tables + reduction
+constexpr size_t SMEM_F32 = (size_t)NV * VS * sizeof(float) + 512 * sizeof(int);   // block + item tables + counters + reduction
 
 // A = c u + F (= 2 F^R) and B = c u - F (= 2 F^L) of one cell for a sweep
 // along AXIS (Eq. LRFlux with w = F/c substituted): c = |v_n| + c_s
@@ -240,13 +240,13 @@ __device__ __forceinline__ int level_of(const SweepArgs<float>& a, int item) {
     return l;
 }
 
-// Threads 0..26 and 32..58 of the block.
-__device__ __forceinline__ void build_tab(ItemTab& t, const SweepArgs<float>& a, int item) {
+// Threads t0..t0+26 and t0+32..t0+58 of the block.
+__device__ __forceinline__ void build_tab(ItemTab& t, const SweepArgs<float>& a, int item, int t0) {
     const int l = level_of(a, item);
     const LevelArgs<float>& L = a.lv[l];
     const int g = item - L.item0;
-    const int tid = threadIdx.x;
-    if (tid < 27) region_entry(L.nbr, g, tid, t.src, t.mask);
+    const int tid = (int)threadIdx.x - t0;
+    if (tid >= 0 && tid < 27) region_entry(L.nbr, g, tid, t.src, t.mask);
     if (tid >= 32 && tid < 59 && L.parent != nullptr)
         region_entry(L.nbrc, L.parent[g] >> 3, tid - 32, t.csrc, t.cmask);
     if (tid == 0) {
@@ -258,6 +258,15 @@ __device__ __forceinline__ void build_tab(ItemTab& t, const SweepArgs<float>& a,
     }
 }
 
+// The interior of a work item into L2 (5 contiguous 16 KiB runs).
+__device__ __forceinline__ void prefetch_item(const SweepArgs<float>& a, int item) {
+    const LevelArgs<float>& L = a.lv[level_of(a, item)];
+    const size_t vs = (size_t)L.n_groups * 8 * 512;
+    const float* b = L.u + ((size_t)(item - L.item0) << 12);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) prefetch_l2(b + v * vs, CELLS_PG * sizeof(float));
+}
+
 __device__ __forceinline__ void prolong_cell(const LevelArgs<float>& L, const ItemTab& t, int x, int y,
                                              int z, float val[NV]) {
     const int lp = t.par & 7;
@@ -266,7 +275,8 @@ __device__ __forceinline__ void prolong_cell(const LevelArgs<float>& L, const It
 }
 
 // One padded x-row (yp, zp) of the block of item t.  SEG bit 0: the 16
-// centre cells (x in [0,16)); bit 1: the 3 + 3 edge cells.  Every cell lies
+// centre cells (x in [0,16)); bit 1: the 3 + 3 edge cells; bit 2 / bit 3:
+// only the first / second half of the centre (one patch row each).  Every cell lies
 // in an aligned quad of a patch row of its source group, so the centre is
 // four 16-byte loads per variable and each edge one.  Outflow edges repeat
 // the centre's edge cell (zero gradient); cells of coarse regions are
@@ -281,22 +291,28 @@ __device__ __forceinline__ void gather_row(float* sm, const SweepArgs<float>& a,
     int xc = 0, yc = y, zc = z;
     const int sc = resolve(t.src, t.mask, xc, yc, zc);
     const size_t offc = sc >= 0 ? cell_offset(sc, 0, yc, zc) : 0;
-    if (SEG & 1) {
+    constexpr bool H0 = (SEG & 1) || (SEG & 4), H1 = (SEG & 1) || (SEG & 8);
+    if (H0 || H1) {
         if (sc >= 0) {
             float4 c[NV][4];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 const float* p = L.u + v * vstride + offc;
-                c[v][0] = ldg4(p);
-                c[v][1] = ldg4(p + 4);
-                c[v][2] = ldg4(p + 512);       // patch px = 1
-                c[v][3] = ldg4(p + 516);
+                if (H0) {
+                    c[v][0] = ldg4(p);
+                    c[v][1] = ldg4(p + 4);
+                }
+                if (H1) {
+                    c[v][2] = ldg4(p + 512);   // patch px = 1
+                    c[v][3] = ldg4(p + 516);
+                }
             }
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 float* q = d + v * VS + NG;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
+                    if ((j < 2 && !H0) || (j >= 2 && !H1)) continue;
                     q[4 * j + 0] = c[v][j].x;
                     q[4 * j + 1] = c[v][j].y;
                     q[4 * j + 2] = c[v][j].z;
@@ -304,7 +320,7 @@ __device__ __forceinline__ void gather_row(float* sm, const SweepArgs<float>& a,
                 }
             }
         } else {
-            for (int x = 0; x < GS; ++x) {
+            for (int x = H0 ? 0 : PS; x < (H1 ? GS : PS); ++x) {
                 float val[NV];
                 prolong_cell(L, t, x, y, z, val);
 #pragma unroll
@@ -371,27 +387,46 @@ __device__ __forceinline__ void gather_row(float* sm, const SweepArgs<float>& a,
 __device__ __forceinline__ int ghost_row(int q) { return q < NG ? q : q + GS; }   // 0..5 -> 0,1,2,19,20,21
 
 template <int ORDER, int PH>
-__device__ __forceinline__ void gather_set(float* sm, const SweepArgs<float>& a, const ItemTab& t,
-                                           int t0, int stride) {
-    constexpr int N = ORDER == 0 ? (PH == 0 ? PD * PD : PH == 1 ? 6 * PD : PH == 2 ? 6 * GS : GS * GS)
-                                 : (PH == 0 ? 6 * PD : PH == 1 ? 6 * GS : GS * GS);
-    for (int r = t0; r < N; r += stride) {
-        int yp, zp;
-        if (ORDER == 0) {
-            if (PH == 0) { yp = r % PD; zp = r / PD; }
-            else if (PH == 1) { yp = ghost_row(r % 6); zp = r / 6; }
-            else if (PH == 2) { yp = NG + r % GS; zp = ghost_row(r / GS); }
-            else { yp = NG + r % GS; zp = NG + r / GS; }
-            if (PH == 0) gather_row<2>(sm, a, t, yp, zp);
-            else gather_row<1>(sm, a, t, yp, zp);
-        } else {
-            if (PH == 0) { yp = r % PD; zp = ghost_row(r / PD); }
-            else if (PH == 1) { yp = ghost_row(r % 6); zp = NG + r / 6; }
-            else { yp = NG + r % GS; zp = NG + r / GS; }
-            if (PH <= 1) gather_row<3>(sm, a, t, yp, zp);
-            else if (PH == 2) gather_row<2>(sm, a, t, yp, zp);
-            else gather_row<1>(sm, a, t, yp, zp);
-        }
+struct GatherSet {
+    static constexpr int N = ORDER == 0 ? (PH == 0 ? PD * PD : PH == 1 ? 6 * PD : PH == 2 ? 6 * GS : 2 * GS * GS)
+                                        : (PH == 0 ? 6 * PD : PH == 1 ? 6 * GS : PH == 2 ? GS * GS : 2 * GS * GS);
+};
+
+// Task r of set PH (set D is split into half rows so that every thread
+// gets one).
+template <int ORDER, int PH>
+__device__ __forceinline__ void gather_task(float* sm, const SweepArgs<float>& a, const ItemTab& t, int r) {
+    if (PH == 3) {
+        const int row = r >> 1;
+        if (r & 1) gather_row<8>(sm, a, t, NG + row % GS, NG + row / GS);
+        else gather_row<4>(sm, a, t, NG + row % GS, NG + row / GS);
+        return;
+    }
+    int yp, zp;
+    if (ORDER == 0) {
+        if (PH == 0) { yp = r % PD; zp = r / PD; }
+        else if (PH == 1) { yp = ghost_row(r % 6); zp = r / 6; }
+        else { yp = NG + r % GS; zp = ghost_row(r / GS); }
+        if (PH == 0) gather_row<2>(sm, a, t, yp, zp);
+        else gather_row<1>(sm, a, t, yp, zp);
+    } else {
+        if (PH == 0) { yp = r % PD; zp = ghost_row(r / PD); }
+        else if (PH == 1) { yp = ghost_row(r % 6); zp = NG + r / 6; }
+        else { yp = NG + r % GS; zp = NG + r / GS; }
+        if (PH <= 1) gather_row<3>(sm, a, t, yp, zp);
+        else gather_row<2>(sm, a, t, yp, zp);
+    }
+}
+
+// Tasks of set PH handed out through a shared-memory counter: threads that
+// finish their own phase work early (sweep columns, store rows) pick up the
+// remaining gather tasks.
+template <int ORDER, int PH>
+__device__ __forceinline__ void gather_pool(float* sm, const SweepArgs<float>& a, const ItemTab& t, int* cnt) {
+    for (;;) {
+        const int r = atomicAdd(cnt, 1);
+        if (r >= GatherSet<ORDER, PH>::N) break;
+        gather_task<ORDER, PH>(sm, a, t, r);
     }
 }
 
@@ -403,72 +438,105 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
     hi = s;
 }
 
-// Interior 16^3 -> u_out, one interior x-row (16 cells) per thread, two
-// aligned 16-byte stores per patch row and variable.  With diagnostics on,
-// the thread also accumulates the exact speed maximum (as the bit pattern
-// of a non-negative float, so a NaN wins), double-float sums of the five
-// variables and the count of bad cells; warps reduce with shuffles and
-// lane 0 parks the warp's result in red[warp][12].
-__device__ __forceinline__ void store_rows(const float* sm, const LevelArgs<float>& L, int g, int t0,
-                                           int stride, bool diag, float gam, float gm1, float* red) {
-    const size_t vstride = (size_t)L.n_groups * 8 * 512;
+// Diagnostic accumulators of one thread: the exact speed maximum as the bit
+// pattern of a non-negative float (a NaN wins), double-float sums of the
+// five variables, the count of bad cells.
+struct DiagAcc {
     unsigned smax = 0u;
-    float hi[NV] = {0.f, 0.f, 0.f, 0.f, 0.f}, lo[NV] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float hi[NV] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float lo[NV] = {0.f, 0.f, 0.f, 0.f, 0.f};
     int bad = 0;
-    for (int r = t0; r < GS * GS; r += stride) {
-        const int y = r % GS, z = r / GS;
-        const float* s = sm + ((z + NG) * PD + (y + NG)) * XP + NG;
-        float* o = L.u_out + cell_offset(g, 0, y, z);
+    __device__ __forceinline__ void add(const float u[NV], float g, float gm1) {
+        float sp, P;
+        speed_pressure_f32(u, g, gm1, sp, P);
+        smax = max(smax, __float_as_uint(sp));
+        bool fin = true;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            df_add(hi[v], lo[v], u[v]);
+            fin = fin && isfinite(u[v]);
+        }
+        bad += (!fin || !(u[0] > 0.0f) || !(P > 0.0f)) ? 1 : 0;
+    }
+    // warp reduction; lane 0 parks the warp's result in red[warp][12]
+    __device__ __forceinline__ void park(float* red) {
+        const unsigned full = 0xffffffffu;
+#pragma unroll
+        for (int w = 16; w > 0; w >>= 1) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const float oh = __shfl_xor_sync(full, hi[v], w), ol = __shfl_xor_sync(full, lo[v], w);
+                df_add(hi[v], lo[v], oh);
+                lo[v] += ol;
+            }
+        }
+        smax = __reduce_max_sync(full, smax);
+        bad = __reduce_add_sync(full, bad);
+        if ((threadIdx.x & 31) == 0) {
+            float* rr = red + (threadIdx.x >> 5) * 12;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                rr[2 * v] = hi[v];
+                rr[2 * v + 1] = lo[v];
+            }
+            rr[10] = __uint_as_float(smax);
+            rr[11] = __int_as_float(bad);
+        }
+    }
+};
+
+// The last sweep of a set: 256 interior lines (z-columns for xyz, x-rows
+// for zyx), one per thread of warps 0..7.  Right after its line the thread
+// writes the 16 finished cells to u_out (x-rows: two aligned 16-byte stores
+// per patch row and variable; z-columns: one store per cell and variable,
+// coalesced across the warp's consecutive x) and, with diagnostics on,
+// accumulates them and parks the warp's result in red.
+template <int ORDER, int LIM>
+__device__ __forceinline__ void sweep_last_store(float* sm, float lam, float g, float gm1, float* flux_g,
+                                                 const LevelArgs<float>& L, int grp, bool diag, float* red) {
+    constexpr int AX = ORDER == 0 ? 2 : 0;
+    constexpr int T1 = AX == 0 ? 1 : 0;
+    constexpr int T2 = AX == 2 ? 1 : 2;
+    constexpr int ST[3] = {1, XP, PD * XP};
+    constexpr int S = ST[AX];
+    const int c = threadIdx.x;               // < 256
+    const int i1 = NG + c % GS, i2 = NG + c / GS;
+    float* p = sm + i1 * ST[T1] + i2 * ST[T2];
+    float* fl = flux_g ? flux_g + AX * (3 * NV * 256) + (i2 - NG) * GS + (i1 - NG) : nullptr;
+    column<AX, S, LIM>(p, 0.25f * lam, 0.5f * lam, g, gm1, fl);
+    const size_t vstride = (size_t)L.n_groups * 8 * 512;
+    DiagAcc acc;
+    if (AX == 0) {
+        float* o = L.u_out + cell_offset(grp, 0, i1 - NG, i2 - NG);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             float u[4][NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) u[q][v] = s[v * VS + 4 * j + q];
+                for (int q = 0; q < 4; ++q) u[q][v] = p[(NG + 4 * j + q) + v * VS];
                 *reinterpret_cast<float4*>(o + v * vstride + (j >> 1) * 512 + (j & 1) * 4) =
                     make_float4(u[0][v], u[1][v], u[2][v], u[3][v]);
             }
             if (diag) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    float sp, P;
-                    speed_pressure_f32(u[q], gam, gm1, sp, P);
-                    smax = max(smax, __float_as_uint(sp));
-                    bool fin = true;
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) {
-                        df_add(hi[v], lo[v], u[q][v]);
-                        fin = fin && isfinite(u[q][v]);
-                    }
-                    bad += (!fin || !(u[q][0] > 0.0f) || !(P > 0.0f)) ? 1 : 0;
-                }
+                for (int q = 0; q < 4; ++q) acc.add(u[q], g, gm1);
             }
         }
-    }
-    if (!diag) return;
-    const unsigned full = 0xffffffffu;
+    } else {
+        float* o = L.u_out + cell_offset(grp, i1 - NG, i2 - NG, 0);
+#pragma unroll 4
+        for (int z = 0; z < GS; ++z) {
+            float u[NV];
 #pragma unroll
-    for (int w = 16; w > 0; w >>= 1) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            const float oh = __shfl_xor_sync(full, hi[v], w), ol = __shfl_xor_sync(full, lo[v], w);
-            df_add(hi[v], lo[v], oh);
-            lo[v] += ol;
+            for (int v = 0; v < NV; ++v) {
+                u[v] = p[(NG + z) * S + v * VS];
+                o[v * vstride + (z >> 3) * 2048 + (z & 7) * 64] = u[v];   // patch pz = z / 8, row z % 8
+            }
+            if (diag) acc.add(u, g, gm1);
         }
     }
-    smax = __reduce_max_sync(full, smax);
-    bad = __reduce_add_sync(full, bad);
-    if ((threadIdx.x & 31) == 0) {
-        float* rr = red + (threadIdx.x >> 5) * 12;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            rr[2 * v] = hi[v];
-            rr[2 * v + 1] = lo[v];
-        }
-        rr[10] = __uint_as_float(smax);
-        rr[11] = __int_as_float(bad);
-    }
+    if (diag) acc.park(red);
 }
 
 // Combine the parked warp results of one item (threads 0..5) and write the
@@ -492,79 +560,103 @@ __device__ __forceinline__ void finish_diag(const DiagSink& d, int item, const f
     }
 }
 
-// Persistent kernel.  NT = 512 threads (16 warps), one CTA per SM.
-//   sweep 1: all warps;
-//   sweep 2: 352 columns on warps 0..10, warps 11..15 gather set A of the
-//            next item;
-//   sweep 3: 256 columns on warps 0..7, warps 8..15 gather set B;
-//   store:   warps 0..7 write the interior, warps 8..15 gather set C;
-//   then all warps gather set D (the next item's interior centres).
-// The first item of each CTA is gathered whole.  Work items come from an
-// atomic counter, one item ahead, whose interior is prefetched into L2.
+// Persistent kernel.  NT = 512 threads (16 warps), one CTA per SM.  Work
+// items (level, group) come from an atomic counter, one ahead.  Per item:
+//   sweep 1: all warps (for xyz each thread first gathers the centre of its
+//            own x-row unless set B already holds it);
+//   sweep 2: 352 columns on warps 0..10; warps 11..15 build the next item's
+//            region tables, prefetch its interior into L2 and gather its set A;
+//   sweep 3: 256 lines on warps 0..7, each thread storing its finished line
+//            (and accumulating the diagnostics); warps 8..15 gather set B;
+//   zyx only: all warps gather the next item's sets C and D.
+// The first item of each CTA is gathered whole.
 constexpr int NT_F32 = 512;
+
+template <int ORDER, int LIM>
+__device__ __forceinline__ void sweep_first(float* sm, const SweepArgs<float>& a, const ItemTab& t,
+                                            float lam, float* flux_g) {
+    if (ORDER == 0) {
+        // x-rows (yp, zp); rows with yp in [3,19) get their centre first
+        const int c = threadIdx.x;
+        if (c >= PD * PD) return;
+        const int yp = c % PD, zp = c / PD;
+        if (yp >= NG && yp < NG + GS) gather_row<1>(sm, a, t, yp, zp);
+        float* p = sm + yp * XP + zp * (PD * XP);
+        float* fl = nullptr;
+        if (flux_g != nullptr && yp >= NG && yp < NG + GS && zp >= NG && zp < NG + GS)
+            fl = flux_g + (zp - NG) * GS + (yp - NG);
+        column<0, 1, LIM>(p, 0.25f * lam, 0.5f * lam, a.gamma, a.gm1, fl);
+    } else {
+        sweep<ORDER, 0, LIM>(sm, lam, a.gamma, a.gm1, flux_g, NT_F32);
+    }
+}
 
 template <int ORDER, int LIM>
 __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> args) {
     extern __shared__ float sm[];
     ItemTab* tab = reinterpret_cast<ItemTab*>(sm + NV * VS);     // [2]
     int* s_item = reinterpret_cast<int*>(tab + 2);               // current, next
-    float* s_red = reinterpret_cast<float*>(s_item + 2);         // [8 warps][12]
+    int* s_cnt = s_item + 2;                                     // gather-set counters A, B
+    float* s_red = reinterpret_cast<float*>(s_cnt + 4);          // [8 warps][12]
     const int tid = threadIdx.x;
     const bool diag = args.diag.pg_max != nullptr;
 
     if (tid == 0) {
         s_item[0] = atomicAdd(args.queue, 1);
         s_item[1] = atomicAdd(args.queue, 1);
+        s_cnt[0] = s_cnt[1] = 0;
     }
     __syncthreads();
     if (s_item[0] >= args.total) return;
     int slot = 0;
-    build_tab(tab[0], args, s_item[0]);
+    build_tab(tab[0], args, s_item[0], 0);
     __syncthreads();
     for (int r = tid; r < PD * PD; r += NT_F32) gather_row<3>(sm, args, tab[0], r % PD, r / PD);
 
     for (;;) {
+        __syncthreads();
         const int next = s_item[1];
         const bool has_next = next < args.total;
-        if (has_next) {
-            build_tab(tab[slot ^ 1], args, next);
-            if (tid == 0) {
-                const LevelArgs<float>& Ln = args.lv[level_of(args, next)];
-                const size_t vs = (size_t)Ln.n_groups * 8 * 512;
-                const int gn = next - Ln.item0;
-                const float* b = Ln.u + ((size_t)gn << 12);
-#pragma unroll
-                for (int v = 0; v < NV; ++v) prefetch_l2(b + v * vs, CELLS_PG * sizeof(float));
-            }
-        }
-        __syncthreads();
         const ItemTab& cur = tab[slot];
-        const ItemTab& nxt = tab[slot ^ 1];
+        ItemTab& nxt = tab[slot ^ 1];
         const LevelArgs<float>& L = args.lv[cur.level];
         float* fg = L.flux ? L.flux + (size_t)cur.g * FLUX_PG : nullptr;
-
         const float lam = cur.lam;
         const int cur_item = cur.item;
+        const int cur_g = cur.g;
 
-        sweep<ORDER, 0, LIM>(sm, lam, args.gamma, args.gm1, fg, NT_F32);
+        sweep_first<ORDER, LIM>(sm, args, cur, lam, fg);
         __syncthreads();
-        if (tid < 11 * 32) sweep<ORDER, 1, LIM>(sm, lam, args.gamma, args.gm1, fg, 11 * 32);
-        else if (has_next) gather_set<ORDER, 0>(sm, args, nxt, tid - 11 * 32, NT_F32 - 11 * 32);
-        __syncthreads();
-        if (tid < 8 * 32) sweep<ORDER, 2, LIM>(sm, lam, args.gamma, args.gm1, fg, 8 * 32);
-        else if (has_next) gather_set<ORDER, 1>(sm, args, nxt, tid - 8 * 32, NT_F32 - 8 * 32);
-        __syncthreads();
-        if (tid < 8 * 32) store_rows(sm, L, cur.g, tid, 8 * 32, diag, args.gamma, args.gm1, s_red);
-        else if (has_next) gather_set<ORDER, 2>(sm, args, nxt, tid - 8 * 32, NT_F32 - 8 * 32);
-        if (tid == 0) {
-            s_item[0] = next;
-            s_item[1] = has_next ? atomicAdd(args.queue, 1) : next;
+        if (tid < 11 * 32) {
+            sweep<ORDER, 1, LIM>(sm, lam, args.gamma, args.gm1, fg, 11 * 32);
+        } else if (has_next) {
+            build_tab(nxt, args, next, 11 * 32);
+            if (tid == 11 * 32) prefetch_item(args, next);
+            asm volatile("bar.sync 1, 160;" ::: "memory");      // warps 11..15: tables ready
+            gather_pool<ORDER, 0>(sm, args, nxt, &s_cnt[0]);
         }
         __syncthreads();
+        if (tid < 8 * 32) {
+            sweep_last_store<ORDER, LIM>(sm, lam, args.gamma, args.gm1, fg, L, cur_g, diag, s_red);
+            if (tid == 0) {
+                s_item[0] = next;
+                s_item[1] = has_next ? atomicAdd(args.queue, 1) : next;
+            }
+        } else if (has_next) {
+            gather_pool<ORDER, 1>(sm, args, nxt, &s_cnt[1]);
+        }
+        __syncthreads();
+        if (tid == 0) s_cnt[0] = s_cnt[1] = 0;
         if (diag) finish_diag(args.diag, cur_item, s_red, 8);
         if (!has_next) break;
         slot ^= 1;
-        gather_set<ORDER, 3>(sm, args, tab[slot], tid, NT_F32);
+        if (ORDER == 1) {
+            // sets C (x-edges of the interior rows) and D (their centres, by halves)
+            for (int r = tid; r < GS * GS + 2 * GS * GS; r += NT_F32) {
+                if (r < GS * GS) gather_row<2>(sm, args, tab[slot], NG + r % GS, NG + r / GS);
+                else gather_task<ORDER, 3>(sm, args, tab[slot], r - GS * GS);
+            }
+        }
     }
 }
 
