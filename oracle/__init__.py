@@ -154,7 +154,9 @@ class OracleLevels:
         self.n = H.n_levels
         if with_flux is None:
             with_flux = self.n > 1
-        self.u = [np.ascontiguousarray(s, dtype=np.float64) for s in states]
+        # private copies: step() ping-pongs between u and u_out and must not
+        # write into the caller's arrays
+        self.u = [np.array(s, dtype=np.float64, order="C", copy=True) for s in states]
         self.u_out = [np.empty_like(s) for s in self.u]
         self.nbr = [np.ascontiguousarray(lv.nbr, dtype=np.int32) for lv in H.levels]
         self.parent = [None if lv.parent is None else np.ascontiguousarray(lv.parent, dtype=np.int32)

@@ -1,0 +1,128 @@
+"""GPU parity at the full sizes of the workloads, in the launch configuration
+the benchmark times (gamer_hydro_step: one persistent FP32 launch or the
+plain FP64 path, then the fix-ups and the diagnostics).
+
+* 512^3 uniform lognormal (262,144 patches): one step; sampled patch groups
+  recomputed by the oracle one by one (its patch-group form reads only the
+  neighbourhood of each group).
+* three-level AMR hierarchy over a 128^3 base (4096 / 9000 / 21000
+  patches): two steps, every cell compared.
+* four-level stress hierarchies (32,768 patches): lognormal sigma 2.5 with
+  Mach-20 flows, and a Sedov point blast: two steps, every cell compared,
+  composite conservation checked.
+
+Tolerances as in test_gpu_parity.py: FP64 bit-identical (and <= 1e-12
+relative), FP32 per-field L1 / max relative to the field's scale.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_0907_3390_gb300 import binding as B  # noqa: E402
+from paper_0907_3390_gb300 import workloads as wl  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+G = 5.0 / 3.0
+CFL = 0.5
+
+
+def rel(gpu, ref):
+    d = np.abs(gpu - ref).reshape(5, -1)
+    scale = np.abs(ref).reshape(5, -1).max(1)
+    scale[scale == 0] = 1.0
+    return d.mean(1) / scale, d.max(1) / scale
+
+
+def gpu_steps(H, st, precision, dtype, n):
+    S = B.Solver(G, B.GAMER_LIMITER_VANLEER, precision)
+    D = B.DeviceHierarchy(H, st, dtype)
+    dts = []
+    for _ in range(n):
+        B.gamer_hydro_step(S.h, D, CFL)
+        D.swap()
+        dts.append(B.gamer_hydro_step_result(S.h)[0])
+    torch.cuda.synchronize()
+    return S, D, dts
+
+
+@pytest.fixture(scope="module")
+def uniform512():
+    u, npg = wl.lognormal_grf(512, seed=1003, dtype=np.float32)
+    H, st = wl.single_level(u, npg)
+    return H, st
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_uniform512_sampled_groups(uniform512, prec):
+    H, st = uniform512
+    p, dt_ = (B.GAMER_FP32, torch.float32) if prec == "f32" else (B.GAMER_FP64, torch.float64)
+    S, D, dts = gpu_steps(H, st, p, dt_, 1)
+    n = H.levels[0].n_groups
+    rng = np.random.default_rng(7)
+    groups = np.unique(np.concatenate([[0, 1, n // 2, n - 1], rng.integers(0, n, 20)])).astype(np.int32)
+    # the oracle receives exactly the values the GPU received
+    src = st[0].astype(np.float32).astype(np.float64) if prec == "f32" else st[0].astype(np.float64)
+    O = oracle.OracleLevels(H, [src], with_flux=False)
+    O.advance_level(0, G, dts[0], 0, groups=groups)
+    out = D.u[0].reshape(5, n, 8, 8, 8, 8)[:, groups].double().cpu().numpy()
+    ref = O.u_out[0].reshape(5, n, 8, 8, 8, 8)[:, groups]
+    L1, mx = rel(out, ref)
+    if prec == "f64":
+        assert mx.max() <= 1e-12, mx
+        assert np.array_equal(out, ref)
+    else:
+        assert L1.max() <= 2e-6 and mx.max() <= 1e-4, (L1, mx)
+    S.close()
+
+
+def amr_compare(H, st, n_steps, f32_tol):
+    # oracle with the GPU's dt sequence
+    S64, D64, dts = gpu_steps(H, st, B.GAMER_FP64, torch.float64, n_steps)
+    O = oracle.OracleLevels(H, st)
+    for k, dt in enumerate(dts):
+        O.step(G, dt, k % 2)
+    for l in range(H.n_levels):
+        got = D64.u[l].cpu().numpy()
+        L1, mx = rel(got, O.u[l])
+        assert mx.max() <= 1e-12, (l, mx)
+        assert np.array_equal(got, O.u[l]), l
+    S64.close()
+    # FP32: the same dt sequence through advance_all, compared level by level
+    S = B.Solver(G, B.GAMER_LIMITER_VANLEER, B.GAMER_FP32)
+    D = B.DeviceHierarchy(H, st, torch.float32)
+    for dt in dts:
+        B.gamer_hydro_advance_all(S.h, D, dt)
+        D.swap()
+    torch.cuda.synchronize()
+    errs = []
+    for l in range(H.n_levels):
+        L1, mx = rel(D.u[l].double().cpu().numpy(), O.u[l])
+        errs.append((L1.max(), mx.max()))
+        print(f"FP32 vs oracle, level {l}: L1 {L1.max():.2e} max {mx.max():.2e}")
+        assert L1.max() <= f32_tol[0] and mx.max() <= f32_tol[1], (l, L1, mx)
+    S.close()
+    return O, errs
+
+
+def test_amr_three_levels_full():
+    H, st = wl.amr_grf()
+    assert H.patch_counts() == [4096, 9000, 21000]
+    amr_compare(H, st, 2, (5e-6, 5e-4))
+
+
+@pytest.mark.parametrize("kind", ["lognormal", "sedov"])
+def test_amr_four_level_stress_full(kind):
+    H, st = wl.amr_stress(kind)
+    assert H.n_levels == 4 and sum(H.patch_counts()) == 32768
+    O, errs = amr_compare(H, st, 2, (1e-4, 5e-2) if kind == "lognormal" else (1e-5, 1e-2))
+    # composite conservation on the GPU over a few more FP64 steps
+    S, D, _ = gpu_steps(H, st, B.GAMER_FP64, torch.float64, 0)
+    s0, _ = B.gamer_hydro_check(S.h, D)
+    for _ in range(4):
+        B.gamer_hydro_step(S.h, D, CFL)
+        D.swap()
+    _, _, s1, nb = B.gamer_hydro_step_result(S.h)
+    assert np.all(np.abs(s1 - s0) / (np.abs(s0) + 1e-3) < 1e-12), (s1 - s0)
+    S.close()
