@@ -210,6 +210,24 @@ int gamer_hydro_diagnose_noalloc(double gamma, int precision, const gamer_hierar
                                  double cfl, void *cuda_stream, double *dt_out, double sums[5],
                                  int64_t *n_bad);
 
+/* Autotuner: times the launch configurations this build offers on the
+ * caller's hierarchy and keeps the fastest for the handle.  FP32 handles
+ * choose between the pipelined persistent kernel (512 threads: the next
+ * work item's ghost slabs gathered by warps idle in sweeps 2 and 3) and the
+ * non-pipelined one (256 or 512 threads per patch group), each with one CTA
+ * per SM or with a balanced grid (fewer CTAs, same number of rounds); FP64
+ * handles choose 128 or 256 threads per patch group.  The timing runs
+ * whole steps with dt = 0, so it overwrites every level's u_out and face
+ * fluxes but never u.  With cache_path given, a line
+ * "<GPU>|<precision>|lim<L>|levels<N>|groups2^<B>=<config>" is looked up
+ * first (no timing when found) and appended after a timing.  Synchronous.
+ * Captured step graphs are discarded. */
+int gamer_hydro_tune(gamer_hydro_t h, const gamer_hierarchy_t *H, const char *cache_path);
+
+/* Human-readable launch configuration of the handle, written into buf
+ * (len bytes, NUL-terminated). */
+int gamer_hydro_get_config(gamer_hydro_t h, char *buf, int len);
+
 /* Profiling hook: CUDA events (cudaEvent_t, created with timing enabled)
  * that every later advance_all / step records immediately before and after
  * its sweep launches, so the caller can time the dominant kernel with

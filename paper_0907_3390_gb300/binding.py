@@ -26,7 +26,8 @@ EXPORTS = [
     "gamer_hydro_set_parity", "gamer_hydro_get_parity", "gamer_hydro_cfl_dt",
     "gamer_hydro_advance", "gamer_hydro_fixup", "gamer_hydro_advance_all",
     "gamer_hydro_check", "gamer_hydro_diagnose", "gamer_hydro_step", "gamer_hydro_step_result",
-    "gamer_hydro_diagnose_noalloc", "gamer_hydro_set_profiling", "gamer_hydro_last_error",
+    "gamer_hydro_diagnose_noalloc", "gamer_hydro_tune", "gamer_hydro_get_config",
+    "gamer_hydro_set_profiling", "gamer_hydro_last_error",
 ]
 
 
@@ -82,6 +83,8 @@ def load(build_if_needed: bool = True) -> C.CDLL:
         L.gamer_hydro_step_result.argtypes = [H, dp, dp, dp, C.POINTER(C.c_int64)]
         L.gamer_hydro_diagnose_noalloc.argtypes = [C.c_double, C.c_int, hp, C.c_double, vp, dp, dp,
                                                    C.POINTER(C.c_int64)]
+        L.gamer_hydro_tune.argtypes = [H, hp, C.c_char_p]
+        L.gamer_hydro_get_config.argtypes = [H, C.c_char_p, C.c_int]
         L.gamer_hydro_set_profiling.argtypes = [H, vp, vp]
         L.gamer_hydro_last_error.argtypes = [H]
         L.gamer_hydro_last_error.restype = C.c_char_p
@@ -183,6 +186,16 @@ def gamer_hydro_diagnose_noalloc(gamma: float, precision: int, H, cfl: float, st
                                                      C.c_void_p(raw) if raw else None, C.byref(dt), sums,
                                                      C.byref(nb)))
     return dt.value, np.array(sums[:]), int(nb.value)
+
+
+def gamer_hydro_tune(h, H, cache_path=None) -> None:
+    _check(h, load().gamer_hydro_tune(h, H.struct(), None if cache_path is None else str(cache_path).encode()))
+
+
+def gamer_hydro_get_config(h) -> str:
+    buf = C.create_string_buffer(256)
+    _check(h, load().gamer_hydro_get_config(h, buf, 256))
+    return buf.value.decode()
 
 
 def gamer_hydro_set_profiling(h, ev_before, ev_after) -> None:

@@ -67,9 +67,13 @@ struct gamer_hydro_s {
     double* d_stage = nullptr;
     int stage_groups = 0;
 
-    // tuning
+    // launch configuration (gamer_hydro_tune may change it)
+    int f32_variant = 0;          // 0 pipelined, 1 non-pipelined
     int sweep_threads = 512;
+    int grid_mode = 0;            // 0: one CTA per SM (capped by items); 1: balanced rounds
+    int f64_threads = 256;
     int f64_chunk = 2048;
+    bool tuned = false;
 
     // whole steps (gamer_hydro_step): captured CUDA graphs keyed by the
     // launch arguments, replayed on the handle's stream
@@ -341,6 +345,17 @@ int check_pointers(gamer_hydro_t h, const gamer_hierarchy_t* H, bool need_out) {
     return GAMER_OK;
 }
 
+// Persistent-kernel grid: one CTA per SM, capped by the number of items;
+// the balanced mode keeps the same number of rounds with fewer CTAs.
+int sweep_grid(const gamer_hydro_s* h, int items) {
+    int g = std::min(items, h->sm_count);
+    if (h->grid_mode == 1 && g > 0) {
+        const int rounds = (items + g - 1) / g;
+        g = (items + rounds - 1) / rounds;
+    }
+    return std::max(g, 1);
+}
+
 int check_level_arg(gamer_hydro_t h, const gamer_hierarchy_t* H, int level) {
     if (level < 0 || level >= H->n_levels) return fail(h, GAMER_ERR_ARG, "level out of range");
     return GAMER_OK;
@@ -362,8 +377,8 @@ int advance_level_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, int l, int o
         a.gamma = (float)h->gamma;
         a.gm1 = (float)(h->gamma - 1.0);
         CK(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), h->stream));
-        const int grid = std::min(a.total, h->sm_count);
-        CK(h, launch_sweep_f32(a, order, h->limiter, h->sweep_threads, grid, h->stream));
+        CK(h, launch_sweep_f32(a, order, h->limiter, h->f32_variant, h->sweep_threads, sweep_grid(h, a.total),
+                               h->stream));
     } else {
         LevelArgs<double> a;
         memset(&a, 0, sizeof(a));
@@ -378,7 +393,7 @@ int advance_level_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, int l, int o
         for (int g0 = 0; g0 < L[l].n_groups; g0 += chunk) {
             const int cnt = std::min(chunk, L[l].n_groups - g0);
             CK(h, launch_pg_f64(a, g0, cnt, order, h->limiter, h->gamma, h->gamma - 1.0, h->d_dt,
-                                h->d_stage, h->stream));
+                                h->d_stage, h->f64_threads, h->stream));
         }
     }
     return GAMER_OK;
@@ -511,7 +526,8 @@ int enqueue_step(gamer_hydro_t h, const gamer_hierarchy_t* H, cudaStream_t st, b
         if (item > 0) {
             cudaError_t e = cudaMemsetAsync(h->d_queue, 0, sizeof(int), st);
             if (e == cudaSuccess && h->prof_ev[0]) e = cudaEventRecord(h->prof_ev[0], st);
-            if (e == cudaSuccess) e = launch_sweep_f32(a, order, h->limiter, h->sweep_threads, std::min(item, h->sm_count), st);
+            if (e == cudaSuccess)
+                e = launch_sweep_f32(a, order, h->limiter, h->f32_variant, h->sweep_threads, sweep_grid(h, item), st);
             if (e == cudaSuccess && h->prof_ev[1]) e = cudaEventRecord(h->prof_ev[1], st);
             if (e != cudaSuccess) r = cuda_fail(h, e, "FP32 sweep launch");
         }
@@ -796,6 +812,111 @@ int gamer_hydro_step_result(gamer_hydro_t h, double* dt_used, double* dt_next, d
     if (sums)
         for (int v = 0; v < NV; ++v) sums[v] = o.sum[v];
     if (n_bad) *n_bad = o.n_bad;
+    return GAMER_OK;
+}
+
+int gamer_hydro_tune(gamer_hydro_t h, const gamer_hierarchy_t* H, const char* cache_path) {
+    if (!h) return GAMER_ERR_ARG;
+    CK(h, cudaSetDevice(h->device));
+    int r = prepare(h, H);
+    if (r) return r;
+    if ((r = check_pointers(h, H, true))) return r;
+    if ((r = check_same_parity(h, H))) return r;
+    cudaDeviceProp prop;
+    CK(h, cudaGetDeviceProperties(&prop, h->device));
+    int bucket = 0;
+    while ((1 << bucket) < h->total_groups) ++bucket;
+    char key[384];
+    snprintf(key, sizeof(key), "%s|%s|lim%d|levels%d|groups2^%d", prop.name,
+             h->precision == GAMER_FP32 ? "fp32" : "fp64", h->limiter, H->n_levels, bucket);
+    for (char* c = key; *c; ++c)
+        if (*c == ' ' || *c == '=') *c = '_';
+    struct Cand { int variant, threads, grid, f64t; };
+    std::vector<Cand> cands;
+    if (h->precision == GAMER_FP32)
+        cands = {{0, 512, 0, 256}, {0, 512, 1, 256}, {1, 512, 0, 256}, {1, 256, 0, 256}, {1, 512, 1, 256}};
+    else
+        cands = {{0, 512, 0, 256}, {0, 512, 0, 128}};
+    auto apply = [&](const Cand& c) {
+        h->f32_variant = c.variant;
+        h->sweep_threads = c.threads;
+        h->grid_mode = c.grid;
+        h->f64_threads = c.f64t;
+    };
+    if (cache_path) {
+        FILE* f = fopen(cache_path, "r");
+        if (f) {
+            char line[512];
+            while (fgets(line, sizeof(line), f)) {
+                char* eq = strrchr(line, '=');
+                if (!eq) continue;
+                *eq = 0;
+                Cand c;
+                if (strcmp(line, key) == 0 && sscanf(eq + 1, "%d,%d,%d,%d", &c.variant, &c.threads, &c.grid, &c.f64t) == 4) {
+                    bool known = false;
+                    for (const Cand& k : cands)
+                        known |= k.variant == c.variant && k.threads == c.threads && k.grid == c.grid && k.f64t == c.f64t;
+                    if (known) {
+                        fclose(f);
+                        apply(c);
+                        h->tuned = true;
+                        drop_graphs(h);
+                        return GAMER_OK;
+                    }
+                }
+            }
+            fclose(f);
+        }
+    }
+    // time every candidate on this hierarchy: dt = 0 keeps the arithmetic
+    // and overwrites u_out (and face fluxes), never u
+    CK(h, launch_set_dt(h->d_dt, 0.0, h->stream));
+    h->dt_ready = false;
+    cudaEvent_t e0, e1;
+    CK(h, cudaEventCreate(&e0));
+    CK(h, cudaEventCreate(&e1));
+    float best = 1e30f;
+    Cand pick = cands[0];
+    for (const Cand& c : cands) {
+        apply(c);
+        float t = 1e30f;
+        for (int rep = 0; rep < 4 && !r; ++rep) {
+            cudaEventRecord(e0, h->stream);
+            r = enqueue_step(h, H, h->stream, false, 0.0);
+            cudaEventRecord(e1, h->stream);
+            if (!r && cudaEventSynchronize(e1) == cudaSuccess) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) t = std::min(t, ms);      // first run is a warm-up
+            }
+        }
+        if (r) break;
+        if (t < best) {
+            best = t;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    apply(pick);
+    drop_graphs(h);
+    if (r) return r;
+    h->tuned = true;
+    if (cache_path) {
+        FILE* f = fopen(cache_path, "a");
+        if (f) {
+            fprintf(f, "%s=%d,%d,%d,%d\n", key, pick.variant, pick.threads, pick.grid, pick.f64t);
+            fclose(f);
+        }
+    }
+    return GAMER_OK;
+}
+
+int gamer_hydro_get_config(gamer_hydro_t h, char* buf, int len) {
+    if (!h || !buf || len <= 0) return GAMER_ERR_ARG;
+    snprintf(buf, (size_t)len, "%s kernel=%s threads=%d grid=%s fp64_threads=%d tuned=%d",
+             h->precision == GAMER_FP32 ? "fp32" : "fp64", h->f32_variant == 0 ? "pipelined" : "simple",
+             h->sweep_threads, h->grid_mode == 0 ? "one-per-SM" : "balanced", h->f64_threads, h->tuned ? 1 : 0);
     return GAMER_OK;
 }
 

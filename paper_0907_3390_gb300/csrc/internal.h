@@ -11,12 +11,15 @@
 namespace gh {
 
 // ---- sweep kernels
-cudaError_t launch_sweep_f32(const SweepArgs<float>& a, int order, int lim, int threads, int grid,
+// variant 0: pipelined (512 threads); 1: non-pipelined (256 or 512 threads)
+cudaError_t launch_sweep_f32(const SweepArgs<float>& a, int order, int lim, int variant, int threads, int grid,
                              cudaStream_t st);
 size_t sweep_f32_smem();
 cudaError_t sweep_f32_init();
+// threads per block: 128 or 256
 cudaError_t launch_pg_f64(const LevelArgs<double>& L, int g0, int count, int order, int lim,
-                          double gamma, double gm1, const double* dt, double* stage, cudaStream_t st);
+                          double gamma, double gm1, const double* dt, double* stage, int threads,
+                          cudaStream_t st);
 size_t stage_f64_bytes_per_group();
 
 // ---- fix-up: coarse level c corrected from fine level c+1

@@ -660,36 +660,101 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> 
     }
 }
 
-template <int ORDER, int LIM>
-static cudaError_t set_smem_attr() {
-    return cudaFuncSetAttribute(k_sweep_f32<ORDER, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)SMEM_F32);
+// Non-pipelined variant (an autotuner candidate): per item, all NT threads
+// gather the whole padded block, then the three sweeps run with every
+// thread, the last one storing its lines; the next item's interior is
+// prefetched into L2 one item ahead.  Simpler and without the set
+// bookkeeping; it can win when a CTA gets about one item.
+template <int ORDER, int LIM, int NT>
+__global__ void __launch_bounds__(NT, 1) k_sweep_f32_simple(const SweepArgs<float> args) {
+    extern __shared__ float sm[];
+    ItemTab* tab = reinterpret_cast<ItemTab*>(sm + NV * VS);
+    int* s_item = reinterpret_cast<int*>(tab + 2);
+    float* s_red = reinterpret_cast<float*>(s_item + 6);
+    const int tid = threadIdx.x;
+    const bool diag = args.diag.pg_max != nullptr;
+    if (tid == 0) {
+        s_item[0] = atomicAdd(args.queue, 1);
+        s_item[1] = atomicAdd(args.queue, 1);
+    }
+    __syncthreads();
+    for (;;) {
+        const int item = s_item[0], next = s_item[1];
+        if (item >= args.total) break;
+        build_tab(tab[0], args, item, 0);
+        if (tid == 0 && next < args.total) prefetch_item(args, next);
+        __syncthreads();
+        const ItemTab& cur = tab[0];
+        const LevelArgs<float>& L = args.lv[cur.level];
+        float* fg = L.flux ? L.flux + (size_t)cur.g * FLUX_PG : nullptr;
+        const float lam = cur.lam;
+        const int cur_item = cur.item, cur_g = cur.g;
+        for (int r = tid; r < PD * PD; r += NT) gather_row<3>(sm, args, cur, r % PD, r / PD);
+        __syncthreads();
+        sweep<ORDER, 0, LIM>(sm, lam, args.gamma, args.gm1, fg, NT);
+        __syncthreads();
+        sweep<ORDER, 1, LIM>(sm, lam, args.gamma, args.gm1, fg, NT);
+        __syncthreads();
+        if (tid < 8 * 32) sweep_last_store<ORDER, LIM>(sm, lam, args.gamma, args.gm1, fg, L, cur_g, diag, s_red);
+        if (tid == 0) {
+            s_item[0] = next;
+            s_item[1] = next < args.total ? atomicAdd(args.queue, 1) : next;
+        }
+        __syncthreads();
+        if (diag) finish_diag(args.diag, cur_item, s_red, 8);
+    }
+}
+
+template <typename K>
+static cudaError_t set_attr(K k) {
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_F32);
 }
 
 // Opt every instantiation into the large dynamic shared memory once per
 // process and device (not a stream operation, so it stays out of graph
 // capture).
 cudaError_t sweep_f32_init() {
-    cudaError_t e = set_smem_attr<0, 0>();
-    if (e == cudaSuccess) e = set_smem_attr<0, 1>();
-    if (e == cudaSuccess) e = set_smem_attr<1, 0>();
-    if (e == cudaSuccess) e = set_smem_attr<1, 1>();
+    cudaError_t e = cudaSuccess;
+    const cudaError_t r[] = {
+        set_attr(k_sweep_f32<0, 0>), set_attr(k_sweep_f32<0, 1>), set_attr(k_sweep_f32<1, 0>),
+        set_attr(k_sweep_f32<1, 1>), set_attr(k_sweep_f32_simple<0, 0, 256>),
+        set_attr(k_sweep_f32_simple<0, 1, 256>), set_attr(k_sweep_f32_simple<1, 0, 256>),
+        set_attr(k_sweep_f32_simple<1, 1, 256>), set_attr(k_sweep_f32_simple<0, 0, 512>),
+        set_attr(k_sweep_f32_simple<0, 1, 512>), set_attr(k_sweep_f32_simple<1, 0, 512>),
+        set_attr(k_sweep_f32_simple<1, 1, 512>)};
+    for (cudaError_t x : r)
+        if (x != cudaSuccess) e = x;
     return e;
 }
 
 template <int ORDER, int LIM>
-static cudaError_t launch_one(const SweepArgs<float>& a, int grid, cudaStream_t st) {
+static cudaError_t launch_pipe(const SweepArgs<float>& a, int grid, cudaStream_t st) {
     k_sweep_f32<ORDER, LIM><<<grid, NT_F32, SMEM_F32, st>>>(a);
     return cudaGetLastError();
 }
 
+template <int ORDER, int LIM, int NT>
+static cudaError_t launch_simple(const SweepArgs<float>& a, int grid, cudaStream_t st) {
+    k_sweep_f32_simple<ORDER, LIM, NT><<<grid, NT, SMEM_F32, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int ORDER, int LIM>
+static cudaError_t launch_variant(const SweepArgs<float>& a, int variant, int threads, int grid, cudaStream_t st) {
+    if (variant == 0 && threads == NT_F32) return launch_pipe<ORDER, LIM>(a, grid, st);
+    if (variant == 1 && threads == 256) return launch_simple<ORDER, LIM, 256>(a, grid, st);
+    if (variant == 1 && threads == 512) return launch_simple<ORDER, LIM, 512>(a, grid, st);
+    return cudaErrorInvalidValue;
+}
+
 size_t sweep_f32_smem() { return SMEM_F32; }
 
-cudaError_t launch_sweep_f32(const SweepArgs<float>& a, int order, int lim, int threads, int grid,
+cudaError_t launch_sweep_f32(const SweepArgs<float>& a, int order, int lim, int variant, int threads, int grid,
                              cudaStream_t st) {
-    if (threads != NT_F32) return cudaErrorInvalidValue;
-    if (order == 0) return lim == 0 ? launch_one<0, 0>(a, grid, st) : launch_one<0, 1>(a, grid, st);
-    return lim == 0 ? launch_one<1, 0>(a, grid, st) : launch_one<1, 1>(a, grid, st);
+    if (order == 0) return lim == 0 ? launch_variant<0, 0>(a, variant, threads, grid, st)
+                                    : launch_variant<0, 1>(a, variant, threads, grid, st);
+    return lim == 0 ? launch_variant<1, 0>(a, variant, threads, grid, st)
+                    : launch_variant<1, 1>(a, variant, threads, grid, st);
 }
 
 }  // namespace gh

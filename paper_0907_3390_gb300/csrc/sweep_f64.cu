@@ -166,10 +166,8 @@ __device__ __forceinline__ void sweep64(double* blk, double lam, double g, doubl
     }
 }
 
-constexpr int NT64 = 256;
-
 // Group g0 + blockIdx.x of level L; scratch block blockIdx.x of `stage`.
-template <int ORDER, int LIM>
+template <int ORDER, int LIM, int NT64>
 __global__ void __launch_bounds__(NT64) k_pg_f64(const LevelArgs<double> L, int g0, double gamma,
                                                   double gm1, const double* __restrict__ dt,
                                                   double* __restrict__ stage) {
@@ -215,17 +213,26 @@ __global__ void __launch_bounds__(NT64) k_pg_f64(const LevelArgs<double> L, int 
 
 size_t stage_f64_bytes_per_group() { return BLK64 * sizeof(double); }
 
-cudaError_t launch_pg_f64(const LevelArgs<double>& L, int g0, int count, int order, int lim,
-                          double gamma, double gm1, const double* dt, double* stage, cudaStream_t st) {
-    if (count <= 0) return cudaSuccess;
+template <int NT>
+static cudaError_t launch_nt(const LevelArgs<double>& L, int g0, int count, int order, int lim, double gamma,
+                             double gm1, const double* dt, double* stage, cudaStream_t st) {
     if (order == 0) {
-        if (lim == 0) k_pg_f64<0, 0><<<count, NT64, 0, st>>>(L, g0, gamma, gm1, dt, stage);
-        else k_pg_f64<0, 1><<<count, NT64, 0, st>>>(L, g0, gamma, gm1, dt, stage);
+        if (lim == 0) k_pg_f64<0, 0, NT><<<count, NT, 0, st>>>(L, g0, gamma, gm1, dt, stage);
+        else k_pg_f64<0, 1, NT><<<count, NT, 0, st>>>(L, g0, gamma, gm1, dt, stage);
     } else {
-        if (lim == 0) k_pg_f64<1, 0><<<count, NT64, 0, st>>>(L, g0, gamma, gm1, dt, stage);
-        else k_pg_f64<1, 1><<<count, NT64, 0, st>>>(L, g0, gamma, gm1, dt, stage);
+        if (lim == 0) k_pg_f64<1, 0, NT><<<count, NT, 0, st>>>(L, g0, gamma, gm1, dt, stage);
+        else k_pg_f64<1, 1, NT><<<count, NT, 0, st>>>(L, g0, gamma, gm1, dt, stage);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_pg_f64(const LevelArgs<double>& L, int g0, int count, int order, int lim,
+                          double gamma, double gm1, const double* dt, double* stage, int threads,
+                          cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    if (threads == 128) return launch_nt<128>(L, g0, count, order, lim, gamma, gm1, dt, stage, st);
+    if (threads == 256) return launch_nt<256>(L, g0, count, order, lim, gamma, gm1, dt, stage, st);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace gh

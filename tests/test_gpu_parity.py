@@ -404,3 +404,43 @@ def test_step_api_amr_conserves():
         tol = 1e-12 if prec is F64 else 1e-6
         assert np.all(np.abs(s1 - s0) / (np.abs(s0) + 1e-3) < tol), (s1 - s0)
         S.close()
+
+
+# ------------------------------------------------------------ autotuner
+
+def _forced(path, key_probe_solver, H, D, cfg):
+    """Write a cache file that forces configuration cfg for this hierarchy."""
+    import re
+    # learn the key by tuning once into a scratch cache file
+    B.gamer_hydro_tune(key_probe_solver.h, D, str(path) + ".probe")
+    key = open(str(path) + ".probe").read().strip().split("=")[0]
+    with open(path, "w") as f:
+        f.write(f"{key}={cfg}\n")
+
+
+@pytest.mark.parametrize("prec", [F32, F64])
+def test_every_tuned_configuration_is_bit_identical(tmp_path, prec):
+    H, st = amr_case()
+    ref = None
+    cands = ["0,512,0,256", "0,512,1,256", "1,512,0,256", "1,256,0,256", "1,512,1,256"] if prec is F32 \
+        else ["0,512,0,256", "0,512,0,128"]
+    for i, cfg in enumerate(cands):
+        S = B.Solver(G, 0, prec[0])
+        D = B.DeviceHierarchy(H, st, prec[1])
+        u_before = [x.clone() for x in D.u]
+        cache = tmp_path / f"tune{i}.txt"
+        _forced(cache, S, H, D, cfg)
+        for a, b in zip(u_before, D.u):
+            assert torch.equal(a, b)              # tuning never writes u
+        B.gamer_hydro_tune(S.h, D, str(cache))    # read back from the cache: no timing
+        assert f"threads={cfg.split(',')[1]}" in B.gamer_hydro_get_config(S.h) or prec is F64
+        for _ in range(3):
+            B.gamer_hydro_step(S.h, D, 0.5)
+            D.swap()
+        out = D.states()
+        if ref is None:
+            ref = out
+        else:
+            for a, b in zip(ref, out):
+                assert np.array_equal(a, b), cfg
+        S.close()
