@@ -160,7 +160,11 @@ int gamer_hydro_advance_all(gamer_hydro_t h, const gamer_hierarchy_t *H, double 
  * any call that set dt from the host) computes dt from the current state
  * first.  The sequence is captured once per (hierarchy version, u/u_out
  * pointers, parity, cfl) as a CUDA graph and replayed on the handle's
- * stream: no host round trip per step.  Asynchronous; the caller swaps u
+ * stream: no host round trip per step.  For a single-level FP32 hierarchy
+ * the graph is one kernel: the CTA of the sweep launch that finishes last
+ * reduces the diagnostics, sets the device dt and writes the step result
+ * to mapped pinned host memory.  A handle's launches share its work-queue
+ * counters, so they must stay ordered on one stream.  Asynchronous; the caller swaps u
  * and u_out afterwards and may read the result with
  * gamer_hydro_step_result. */
 int gamer_hydro_step(gamer_hydro_t h, const gamer_hierarchy_t *H, double cfl);

@@ -204,7 +204,6 @@ __global__ void __launch_bounds__(NT_DIAG) k_diag(const DiagArgs<T> a) {
 
 // One block per level: combine the per-group results of the level in a
 // fixed order (strided partials, then a fixed tree).
-constexpr int NT_FIN = 256;
 template <typename T>
 __global__ void __launch_bounds__(NT_FIN) k_diag_final(const DiagArgs<T> a) {
     const int l = blockIdx.x;
@@ -275,80 +274,21 @@ cudaError_t launch_set_dt(double* slot, double dt, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-struct LevelMeta {
-    int item0[MAXLEV];
-    int n[MAXLEV];
-    double dh[MAXLEV];
-    int n_levels;
-};
-
-// One block: per level, the per-group results in fixed order (strided
-// partials, fixed tree); then Eq. CFL dt = cfl * min_l dh_l / s_l in FP64
-// and the leaf sums times dh^3, level by level.  *dt becomes the new value
-// when update_dt is set (the next step is an xyz step), otherwise it is
-// held (reading of Sec. 2.2: one dt for a forward and backward sweep).
+// One block: the end-of-step reduction (step_reduce.cuh) as its own launch,
+// for multi-level and FP64 steps.
 __global__ void __launch_bounds__(NT_FIN) k_step_final(const LevelMeta m, const unsigned long long* pg_max,
                                                       const double* pg_sum, const int* pg_bad, double cfl,
-                                                      double* dt, int update_dt, StepOut* out) {
-    __shared__ double s_sum[NV][NT_FIN];
+                                                      double* dt, int update_dt, StepOut* out,
+                                                      StepOut* out_host) {
+    __shared__ double s_sum[NV * NT_FIN];
     __shared__ unsigned long long s_max[NT_FIN];
     __shared__ long long s_bad[NT_FIN];
-    double tot[NV] = {0, 0, 0, 0, 0};
-    double dtc = INFINITY;
-    long long nb = 0;
-    const double dt_used = *dt;
-    for (int l = 0; l < m.n_levels; ++l) {
-        double sum[NV] = {0, 0, 0, 0, 0};
-        unsigned long long mx = 0ull;
-        long long bad = 0;
-        for (int i = threadIdx.x; i < m.n[l]; i += NT_FIN) {
-            const int it = m.item0[l] + i;
-#pragma unroll
-            for (int v = 0; v < NV; ++v) sum[v] += pg_sum[(size_t)it * NV + v];
-            mx = max(mx, pg_max[it]);
-            bad += pg_bad[it];
-        }
-#pragma unroll
-        for (int v = 0; v < NV; ++v) s_sum[v][threadIdx.x] = sum[v];
-        s_max[threadIdx.x] = mx;
-        s_bad[threadIdx.x] = bad;
-        __syncthreads();
-        for (int w = NT_FIN / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w) {
-#pragma unroll
-                for (int v = 0; v < NV; ++v) s_sum[v][threadIdx.x] += s_sum[v][threadIdx.x + w];
-                s_max[threadIdx.x] = max(s_max[threadIdx.x], s_max[threadIdx.x + w]);
-                s_bad[threadIdx.x] += s_bad[threadIdx.x + w];
-            }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0 && m.n[l] > 0) {
-            const double dV = m.dh[l] * m.dh[l] * m.dh[l];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) tot[v] += s_sum[v][0] * dV;
-            const double s = __longlong_as_double((long long)s_max[0]);
-            const double d = m.dh[l] / s;
-            if (d < dtc || d != d) dtc = d;
-            nb += s_bad[0];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const double dnew = cfl * dtc;
-        out->dt_used = dt_used;
-        out->dt_cfl = dnew;
-        out->dt_next = update_dt ? dnew : dt_used;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) out->sum[v] = tot[v];
-        out->n_bad = nb;
-        out->steps += 1;
-        if (update_dt) *dt = dnew;
-    }
+    step_reduce(m, pg_max, pg_sum, pg_bad, cfl, dt, update_dt, out, out_host, s_sum, s_max, s_bad);
 }
 
 cudaError_t launch_step_final(const DiagArgs<float>& a32, const DiagArgs<double>& a64, bool fp64,
                               const double* dh, double cfl, double* dt, int update_dt, StepOut* out,
-                              cudaStream_t st) {
+                              StepOut* out_host, cudaStream_t st) {
     LevelMeta m;
     m.n_levels = fp64 ? a64.n_levels : a32.n_levels;
     for (int l = 0; l < m.n_levels; ++l) {
@@ -359,7 +299,7 @@ cudaError_t launch_step_final(const DiagArgs<float>& a32, const DiagArgs<double>
     const unsigned long long* pm = fp64 ? a64.pg_max : a32.pg_max;
     const double* ps = fp64 ? a64.pg_sum : a32.pg_sum;
     const int* pb = fp64 ? a64.pg_bad : a32.pg_bad;
-    k_step_final<<<1, NT_FIN, 0, st>>>(m, pm, ps, pb, cfl, dt, update_dt, out);
+    k_step_final<<<1, NT_FIN, 0, st>>>(m, pm, ps, pb, cfl, dt, update_dt, out, out_host);
     return cudaGetLastError();
 }
 

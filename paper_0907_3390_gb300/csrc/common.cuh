@@ -46,14 +46,30 @@ struct DiagSink {
     int* pg_bad;
 };
 
+struct StepOut;
+
+// End-of-step reduction run by the CTA that finishes last in a
+// single-level launch with fused diagnostics; out == nullptr turns it off.
+struct StepSink {
+    StepOut* out;       // device copy of the result
+    StepOut* out_host;  // mapped pinned host copy, or nullptr
+    double* dt;         // the launch's dt slot, rewritten after every item is done
+    double cfl;
+    double dh;
+    int update_dt;
+};
+
 template <typename T>
 struct SweepArgs {
     LevelArgs<T> lv[MAXLEV];
     int n_levels;
     int total;          // work items (patch groups) over all levels
     int* queue;         // device work-queue counter, zero before launch
+    unsigned* done;     // count of CTAs that finished, zero before launch; the
+                        // last CTA sets both back to zero
     const double* dt;   // device slot holding the time step
     DiagSink diag;      // fused diagnostics of the new state, or all null
+    StepSink step;      // fused end-of-step reduction (needs diag), or all null
     T gamma;
     T gm1;              // gamma - 1, formed once on the host in FP64
 };

@@ -84,7 +84,8 @@ struct gamer_hydro_s {
     bool dt_ready = false;        // d_dt holds the step dt of the current state
     uint64_t dt_version = 0;
     StepOut* d_step = nullptr;    // device result of the last step
-    StepOut* h_step = nullptr;    // pinned host copy, written by the graph
+    StepOut* h_step = nullptr;    // mapped pinned host copy, written by the step's last kernel
+    StepOut* h_step_dev = nullptr;// the same memory as the device addresses it
     cudaEvent_t step_event = nullptr;
     cudaEvent_t prof_ev[2] = {nullptr, nullptr};   // recorded around the sweep launch
 };
@@ -373,10 +374,10 @@ int advance_level_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, int l, int o
         a.n_levels = 1;
         a.total = L[l].n_groups;
         a.queue = h->d_queue;
+        a.done = reinterpret_cast<unsigned*>(h->d_queue + 1);
         a.dt = h->d_dt;
         a.gamma = (float)h->gamma;
         a.gm1 = (float)(h->gamma - 1.0);
-        CK(h, cudaMemsetAsync(h->d_queue, 0, sizeof(int), h->stream));
         CK(h, launch_sweep_f32(a, order, h->limiter, h->f32_variant, h->sweep_threads, sweep_grid(h, a.total),
                                h->stream));
     } else {
@@ -505,6 +506,7 @@ int enqueue_step(gamer_hydro_t h, const gamer_hierarchy_t* H, cudaStream_t st, b
     h->stream = st;
     int r = GAMER_OK;
     const bool fused = with_diag && h->precision == GAMER_FP32 && n == 1;
+    bool reduced = false;   // the sweep launch runs the end-of-step reduction itself
     DiagArgs<float> d32;
     DiagArgs<double> d64;
     if (h->precision == GAMER_FP32) {
@@ -519,13 +521,18 @@ int enqueue_step(gamer_hydro_t h, const gamer_hierarchy_t* H, cudaStream_t st, b
         a.n_levels = n;
         a.total = item;
         a.queue = h->d_queue;
+        a.done = reinterpret_cast<unsigned*>(h->d_queue + 1);
         a.dt = h->d_dt;
         a.gamma = (float)h->gamma;
         a.gm1 = (float)(h->gamma - 1.0);
         if (fused) a.diag = DiagSink{h->d_pg_max, h->d_pg_sum, h->d_pg_bad};
+        // the next step is an xyz step exactly when this one is zyx
+        reduced = fused && item > 0;
+        if (reduced)
+            a.step = StepSink{h->d_step, h->h_step_dev, h->d_dt, cfl, H->levels[0].dh, order == 1};
         if (item > 0) {
-            cudaError_t e = cudaMemsetAsync(h->d_queue, 0, sizeof(int), st);
-            if (e == cudaSuccess && h->prof_ev[0]) e = cudaEventRecord(h->prof_ev[0], st);
+            cudaError_t e = cudaSuccess;
+            if (h->prof_ev[0]) e = cudaEventRecord(h->prof_ev[0], st);
             if (e == cudaSuccess)
                 e = launch_sweep_f32(a, order, h->limiter, h->f32_variant, h->sweep_threads, sweep_grid(h, item), st);
             if (e == cudaSuccess && h->prof_ev[1]) e = cudaEventRecord(h->prof_ev[1], st);
@@ -560,12 +567,9 @@ int enqueue_step(gamer_hydro_t h, const gamer_hierarchy_t* H, cudaStream_t st, b
         if (!fused)
             e = h->precision == GAMER_FP32 ? launch_diag_groups<float>(d32, h->total_groups, st)
                                            : launch_diag_groups<double>(d64, h->total_groups, st);
-        // the step after this one is an xyz step exactly when this one is zyx
-        if (e == cudaSuccess)
+        if (e == cudaSuccess && !reduced)
             e = launch_step_final(d32, d64, h->precision == GAMER_FP64, dh, cfl, h->d_dt, order == 1,
-                                  h->d_step, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(h->h_step, h->d_step, sizeof(StepOut), cudaMemcpyDeviceToHost, st);
+                                  h->d_step, h->h_step_dev, st);
         if (e != cudaSuccess) r = cuda_fail(h, e, "step diagnostics");
     }
     h->stream = saved;
@@ -582,7 +586,9 @@ int diagnose_to_device(gamer_hydro_t h, const gamer_hierarchy_t* H, double cfl) 
     for (int l = 0; l < H->n_levels; ++l) dh[l] = H->levels[l].dh;
     cudaError_t e = h->precision == GAMER_FP32 ? launch_diag_groups<float>(d32, h->total_groups, h->stream)
                                                : launch_diag_groups<double>(d64, h->total_groups, h->stream);
-    if (e == cudaSuccess) e = launch_step_final(d32, d64, h->precision == GAMER_FP64, dh, cfl, h->d_dt, 1, h->d_step, h->stream);
+    if (e == cudaSuccess)
+        e = launch_step_final(d32, d64, h->precision == GAMER_FP64, dh, cfl, h->d_dt, 1, h->d_step, nullptr,
+                              h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "initial CFL time step");
     return GAMER_OK;
 }
@@ -609,12 +615,16 @@ int gamer_hydro_create(double gamma, int limiter, int ghost_width, int precision
     h->precision = precision;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_queue, sizeof(int));
+    // work-queue counter and finished-CTA counter: zeroed once here, set back
+    // to zero by the last CTA of every FP32 sweep launch
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_queue, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->d_queue, 0, 2 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_dt, sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_step, sizeof(StepOut));
     if (e == cudaSuccess) e = cudaMemset(h->d_step, 0, sizeof(StepOut));
-    if (e == cudaSuccess) e = cudaMallocHost(&h->h_step, sizeof(StepOut));
+    if (e == cudaSuccess) e = cudaHostAlloc(&h->h_step, sizeof(StepOut), cudaHostAllocMapped);
     if (e == cudaSuccess) memset(h->h_step, 0, sizeof(StepOut));
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&h->h_step_dev, h->h_step, 0);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->step_event, cudaEventDisableTiming);
     if (e == cudaSuccess) e = sweep_f32_init();
     if (e != cudaSuccess) {

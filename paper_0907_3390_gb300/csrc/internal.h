@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "step_reduce.cuh"
 
 namespace gh {
 
@@ -68,20 +69,11 @@ cudaError_t launch_diag(const DiagArgs<T>& a, int total, cudaStream_t st);
 template <typename T>
 cudaError_t launch_diag_groups(const DiagArgs<T>& a, int total, cudaStream_t st);
 
-// Result of one whole step, written on the device.
-struct StepOut {
-    double dt_used;     // dt of the step just taken
-    double dt_next;     // dt the next step will use (held for a zyx step)
-    double dt_cfl;      // Eq. CFL from the new state
-    double sum[NV];     // leaf sums of u * dh^3
-    long long n_bad;
-    long long steps;
-};
 // One block: per-level reduction of the per-group diagnostics in fixed
 // order, then dt from Eq. CFL (written to *dt when update_dt != 0).
 cudaError_t launch_step_final(const DiagArgs<float>& a32, const DiagArgs<double>& a64, bool fp64,
                               const double* dh, double cfl, double* dt, int update_dt,
-                              StepOut* out, cudaStream_t st);
+                              StepOut* out, StepOut* out_host, cudaStream_t st);
 cudaError_t launch_set_dt(double* slot, double dt, cudaStream_t st);
 
 // Message of the last failed handle-free call on this thread (read back by

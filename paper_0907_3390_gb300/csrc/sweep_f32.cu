@@ -66,18 +66,19 @@ __device__ __forceinline__ void state(const float u[NV], float g, float gm1, flo
     }
 }
 
-// psi(x, y) = 2 phi(x/4, y/4): by homogeneity of the limiter, on unhalved
-// differences of A or B.  van Leer (Eq. vanLeer): xy/(x+y) when xy > 0;
-// minmod: min(|x|,|y|)/2 with the common sign; zero otherwise.
+// base + s psi(x, y), s = +1 or -1, with psi(x, y) = 2 phi(x/4, y/4): by
+// homogeneity of the limiter, on unhalved differences of A or B.  van Leer
+// (Eq. vanLeer): xy/(x+y) when xy > 0, here as one FMA of xy with
+// s/(x+y); minmod: min(|x|,|y|)/2 with the common sign; zero otherwise.
 template <int LIM>
-__device__ __forceinline__ float psi(float x, float y) {
+__device__ __forceinline__ float add_psi(float base, float x, float y, float s) {
     const float p = x * y;
     if (LIM == 0) {
-        const float q = __fdividef(p, x + y);
-        return p > 0.0f ? q : 0.0f;
+        const float r = __fdividef(s, x + y);
+        return p > 0.0f ? fmaf(p, r, base) : base;
     } else {
         const float m = 0.5f * fminf(fabsf(x), fabsf(y));
-        return p > 0.0f ? copysignf(m, x) : 0.0f;
+        return p > 0.0f ? base + s * copysignf(m, x) : base;
     }
 }
 
@@ -127,8 +128,8 @@ __device__ __forceinline__ void col_step(float* __restrict__ p, int k, ColState&
                     float G[NV];
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
-                        const float Ah = c.Aq[v] + psi<LIM>(c.dAp[v], dA[v]);
-                        const float Bh = c.Bq[v] - psi<LIM>(dB[v], c.dBp[v]);
+                        const float Ah = add_psi<LIM>(c.Aq[v], c.dAp[v], dA[v], 1.0f);
+                        const float Bh = add_psi<LIM>(c.Bq[v], dB[v], c.dBp[v], -1.0f);
                         G[v] = c.Ahp[v] - Bh;                    // net flux (x2) at k-5/2
                         c.Ahp[v] = Ah;
                     }
@@ -560,6 +561,37 @@ __device__ __forceinline__ void finish_diag(const DiagSink& d, int item, const f
     }
 }
 
+// Called by every thread of a CTA once its item loop is over.  Each thread
+// makes its own writes visible device-wide, then the CTA counts itself.  The
+// last CTA to arrive has every other CTA's results in view and the work
+// queue to itself (the others have left their loops): it sets the queue and
+// the counter back to zero for the next launch and, with the fused step
+// reduction on, combines the per-group results of the whole launch (the
+// block's shared memory is free by then).
+__device__ __forceinline__ void finish_launch(const SweepArgs<float>& a, float* sm, int* s_last) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) *s_last = atomicAdd(a.done, 1u) == gridDim.x - 1u ? 1 : 0;
+    __syncthreads();
+    if (*s_last == 0) return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        *a.queue = 0;
+        *a.done = 0u;
+    }
+    if (a.step.out == nullptr) return;
+    LevelMeta m;
+    m.n_levels = 1;
+    m.item0[0] = 0;
+    m.n[0] = a.total;
+    m.dh[0] = a.step.dh;
+    double* s_sum = reinterpret_cast<double*>(sm);
+    unsigned long long* s_max = reinterpret_cast<unsigned long long*>(s_sum + NV * NT_FIN);
+    long long* s_bad = reinterpret_cast<long long*>(s_max + NT_FIN);
+    step_reduce(m, a.diag.pg_max, a.diag.pg_sum, a.diag.pg_bad, a.step.cfl, a.step.dt, a.step.update_dt,
+                a.step.out, a.step.out_host, s_sum, s_max, s_bad);
+}
+
 // Persistent kernel.  NT = 512 threads (16 warps), one CTA per SM.  Work
 // items (level, group) come from an atomic counter, one ahead.  Per item:
 //   sweep 1: all warps (for xyz each thread first gathers the centre of its
@@ -596,7 +628,7 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> 
     extern __shared__ float sm[];
     ItemTab* tab = reinterpret_cast<ItemTab*>(sm + NV * VS);     // [2]
     int* s_item = reinterpret_cast<int*>(tab + 2);               // current, next
-    int* s_cnt = s_item + 2;                                     // gather-set counters A, B
+    int* s_cnt = s_item + 2;                                     // gather-set counters A, B; last-CTA flag
     float* s_red = reinterpret_cast<float*>(s_cnt + 4);          // [8 warps][12]
     const int tid = threadIdx.x;
     const bool diag = args.diag.pg_max != nullptr;
@@ -607,57 +639,60 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> 
         s_cnt[0] = s_cnt[1] = 0;
     }
     __syncthreads();
-    if (s_item[0] >= args.total) return;
-    int slot = 0;
-    build_tab(tab[0], args, s_item[0], 0);
-    __syncthreads();
-    for (int r = tid; r < PD * PD; r += NT_F32) gather_row<3>(sm, args, tab[0], r % PD, r / PD);
+    do {
+        if (s_item[0] >= args.total) break;
+        int slot = 0;
+        build_tab(tab[0], args, s_item[0], 0);
+        __syncthreads();
+        for (int r = tid; r < PD * PD; r += NT_F32) gather_row<3>(sm, args, tab[0], r % PD, r / PD);
 
-    for (;;) {
-        __syncthreads();
-        const int next = s_item[1];
-        const bool has_next = next < args.total;
-        const ItemTab& cur = tab[slot];
-        ItemTab& nxt = tab[slot ^ 1];
-        const LevelArgs<float>& L = args.lv[cur.level];
-        float* fg = L.flux ? L.flux + (size_t)cur.g * FLUX_PG : nullptr;
-        const float lam = cur.lam;
-        const int cur_item = cur.item;
-        const int cur_g = cur.g;
+        for (;;) {
+            __syncthreads();
+            const int next = s_item[1];
+            const bool has_next = next < args.total;
+            const ItemTab& cur = tab[slot];
+            ItemTab& nxt = tab[slot ^ 1];
+            const LevelArgs<float>& L = args.lv[cur.level];
+            float* fg = L.flux ? L.flux + (size_t)cur.g * FLUX_PG : nullptr;
+            const float lam = cur.lam;
+            const int cur_item = cur.item;
+            const int cur_g = cur.g;
 
-        sweep_first<ORDER, LIM>(sm, args, cur, lam, fg);
-        __syncthreads();
-        if (tid < 11 * 32) {
-            sweep<ORDER, 1, LIM>(sm, lam, args.gamma, args.gm1, fg, 11 * 32);
-        } else if (has_next) {
-            build_tab(nxt, args, next, 11 * 32);
-            if (tid == 11 * 32) prefetch_item(args, next);
-            asm volatile("bar.sync 1, 160;" ::: "memory");      // warps 11..15: tables ready
-            gather_pool<ORDER, 0>(sm, args, nxt, &s_cnt[0]);
-        }
-        __syncthreads();
-        if (tid < 8 * 32) {
-            sweep_last_store<ORDER, LIM>(sm, lam, args.gamma, args.gm1, fg, L, cur_g, diag, s_red);
-            if (tid == 0) {
-                s_item[0] = next;
-                s_item[1] = has_next ? atomicAdd(args.queue, 1) : next;
+            sweep_first<ORDER, LIM>(sm, args, cur, lam, fg);
+            __syncthreads();
+            if (tid < 11 * 32) {
+                sweep<ORDER, 1, LIM>(sm, lam, args.gamma, args.gm1, fg, 11 * 32);
+            } else if (has_next) {
+                build_tab(nxt, args, next, 11 * 32);
+                if (tid == 11 * 32) prefetch_item(args, next);
+                asm volatile("bar.sync 1, 160;" ::: "memory");      // warps 11..15: tables ready
+                gather_pool<ORDER, 0>(sm, args, nxt, &s_cnt[0]);
             }
-        } else if (has_next) {
-            gather_pool<ORDER, 1>(sm, args, nxt, &s_cnt[1]);
-        }
-        __syncthreads();
-        if (tid == 0) s_cnt[0] = s_cnt[1] = 0;
-        if (diag) finish_diag(args.diag, cur_item, s_red, 8);
-        if (!has_next) break;
-        slot ^= 1;
-        if (ORDER == 1) {
-            // sets C (x-edges of the interior rows) and D (their centres, by halves)
-            for (int r = tid; r < GS * GS + 2 * GS * GS; r += NT_F32) {
-                if (r < GS * GS) gather_row<2>(sm, args, tab[slot], NG + r % GS, NG + r / GS);
-                else gather_task<ORDER, 3>(sm, args, tab[slot], r - GS * GS);
+            __syncthreads();
+            if (tid < 8 * 32) {
+                sweep_last_store<ORDER, LIM>(sm, lam, args.gamma, args.gm1, fg, L, cur_g, diag, s_red);
+                if (tid == 0) {
+                    s_item[0] = next;
+                    s_item[1] = has_next ? atomicAdd(args.queue, 1) : next;
+                }
+            } else if (has_next) {
+                gather_pool<ORDER, 1>(sm, args, nxt, &s_cnt[1]);
+            }
+            __syncthreads();
+            if (tid == 0) s_cnt[0] = s_cnt[1] = 0;
+            if (diag) finish_diag(args.diag, cur_item, s_red, 8);
+            if (!has_next) break;
+            slot ^= 1;
+            if (ORDER == 1) {
+                // sets C (x-edges of the interior rows) and D (their centres, by halves)
+                for (int r = tid; r < GS * GS + 2 * GS * GS; r += NT_F32) {
+                    if (r < GS * GS) gather_row<2>(sm, args, tab[slot], NG + r % GS, NG + r / GS);
+                    else gather_task<ORDER, 3>(sm, args, tab[slot], r - GS * GS);
+                }
             }
         }
-    }
+    } while (false);
+    finish_launch(args, sm, &s_cnt[2]);
 }
 
 // Non-pipelined variant (an autotuner candidate): per item, all NT threads
@@ -670,7 +705,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f32_simple(const SweepArgs<floa
     extern __shared__ float sm[];
     ItemTab* tab = reinterpret_cast<ItemTab*>(sm + NV * VS);
     int* s_item = reinterpret_cast<int*>(tab + 2);
-    float* s_red = reinterpret_cast<float*>(s_item + 6);
+    float* s_red = reinterpret_cast<float*>(s_item + 6);       // s_item[2]: last-CTA flag
     const int tid = threadIdx.x;
     const bool diag = args.diag.pg_max != nullptr;
     if (tid == 0) {
@@ -703,6 +738,7 @@ __global__ void __launch_bounds__(NT, 1) k_sweep_f32_simple(const SweepArgs<floa
         __syncthreads();
         if (diag) finish_diag(args.diag, cur_item, s_red, 8);
     }
+    finish_launch(args, sm, &s_item[2]);
 }
 
 template <typename K>
