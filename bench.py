@@ -97,7 +97,7 @@ def measured_peaks():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("sweep_f32.cu", "common.cuh"):
+    for f in ("sweep_f32.cu", "common.cuh", "step_reduce.cuh"):
         with open(os.path.join(ROOT, "paper_0907_3390_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -323,33 +323,62 @@ def run_ours(args, rank, world, dist):
 
 def run_extras(args, B, torch, H, st, cells, dev, stream):
     out = {}
-    # ---- e2e through the C ABI with host buffers: every step copies the
-    # state in from pinned host memory, takes the step (its last kernel
-    # writes the step result to mapped host memory) and copies the new state out
-    S = B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP32, stream=stream)
-    D = B.DeviceHierarchy(H, st, torch.float32, device=dev)
-    host_in = [x.cpu().pin_memory() for x in D.u]
-    host_out = [torch.empty_like(x).pin_memory() for x in host_in]
-    n_e2e = max(3, min(args.steps, 10))
+    # ---- e2e through the C ABI with host buffers.  Every step takes its
+    # input state from pinned host memory, advances it one step through
+    # gamer_hydro_step (whose last kernel writes the step result to mapped
+    # host memory) and copies the new state back to pinned host memory.
+    # Two independent states are in flight (double buffering, one handle
+    # each): the copy-in of step k+1 (own stream) overlaps the compute of
+    # step k (the launch stream) and the copy-out of step k-1 (own stream),
+    # as a serving loop over independent states would run.
+    s_in = torch.cuda.Stream(device=dev)
+    s_out = torch.cuda.Stream(device=dev)
+    solvers = [B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP32, stream=stream) for _ in range(2)]
+    bufs = [B.DeviceHierarchy(H, st, torch.float32, device=dev) for _ in range(2)]
+    host_in = [x.cpu().pin_memory() for x in bufs[0].u]
+    host_out = [[torch.empty_like(x).pin_memory() for x in host_in] for _ in range(2)]
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_step = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
+    n_e2e = max(4, min(2 * args.steps, 20))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for it in range(2 + n_e2e):
-        if it == 2:
+    warm = 4
+    for it in range(warm + n_e2e):
+        if it == warm:
             torch.cuda.synchronize()
             e0.record(stream)
-        for l in range(len(D.u)):
-            D.u[l].copy_(host_in[l], non_blocking=True)
+            s_in.wait_stream(stream)             # the first timed copy-in starts after e0
+        b = it % 2
+        S, D = solvers[b], bufs[b]
+        if it >= 2:
+            s_in.wait_event(ev_step[b])          # the previous step on this buffer has read u
+        with torch.cuda.stream(s_in):
+            for l in range(len(D.u)):
+                D.u[l].copy_(host_in[l], non_blocking=True)
+            ev_in[b].record(s_in)
+        stream.wait_event(ev_in[b])
+        if it >= 2:
+            stream.wait_event(ev_out[b])         # u_out of this buffer has been copied out
         B.gamer_hydro_step(S.h, D, CFL)
-        D.swap()
-        for l in range(len(D.u)):
-            host_out[l].copy_(D.u[l], non_blocking=True)
+        ev_step[b].record(stream)
+        s_out.wait_event(ev_step[b])
+        with torch.cuda.stream(s_out):
+            for l in range(len(D.u)):
+                host_out[b][l].copy_(D.u_out[l], non_blocking=True)
+            ev_out[b].record(s_out)
+    stream.wait_event(ev_out[0])
+    stream.wait_event(ev_out[1])
     e1.record(stream)
     torch.cuda.synchronize()
-    B.gamer_hydro_step_result(S.h)
+    for S in solvers:
+        B.gamer_hydro_step_result(S.h)
     ms = e0.elapsed_time(e1) / n_e2e
     nbytes = sum(x.numel() * 4 for x in host_in)
     out["e2e"] = {"value": cells / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                  "d2h_bytes_per_step": nbytes + 96}
-    S.close()
+                  "d2h_bytes_per_step": nbytes + 96,
+                  "pipeline": "2 independent states in flight; copy-in, step and copy-out on 3 streams"}
+    for S in solvers:
+        S.close()
 
     # ---- plain FP64 GPU path (one block per patch group, same whole-step
     # API) and the per-field L1 error of one FP32 sweep set against it (the

@@ -31,6 +31,7 @@
 // with -prec-div=false -prec-sqrt=false -ftz=true).
 #include "common.cuh"
 #include "internal.h"
+#include "lane_maps.h"
 
 namespace gh {
 
@@ -191,6 +192,15 @@ __device__ __forceinline__ void column(float* __restrict__ p, float lam4, float 
     for (int k = 6; k < PD; ++k) col_step<AXIS, S, LIM, 6>(p, k, c, lam4, lam2, g, gm1, fl);
 }
 
+// Column order of sweep S_IDX of an ORDER set that avoids shared-memory
+// bank conflicts within a warp (lane_maps.h), or nullptr where the natural
+// order is kept.
+template <int ORDER, int S_IDX>
+__device__ __forceinline__ const unsigned short* lane_map() {
+    if (ORDER == 0) return S_IDX == 1 ? kLaneXyzS2 : nullptr;
+    return S_IDX == 0 ? kLaneZyxS1 : S_IDX == 1 ? kLaneZyxS2 : kLaneZyxS3;
+}
+
 // Sweep s (0,1,2) of order ORDER over the shared block; columns whose
 // transverse axes were swept earlier in this set only cover [3,19).
 template <int ORDER, int S_IDX, int LIM>
@@ -207,8 +217,17 @@ __device__ __forceinline__ void sweep(float* sm, float lam, float g, float gm1, 
     constexpr int S = ST[AX];
     const float lam4 = 0.25f * lam, lam2 = 0.5f * lam;
     if ((int)threadIdx.x >= nact) return;
+    const unsigned short* map = lane_map<ORDER, S_IDX>();
     for (int c = threadIdx.x; c < N1 * N2; c += nact) {
-        const int i1 = LO1 + c % N1, i2 = LO2 + c / N1;
+        int i1, i2;
+        if (map != nullptr) {
+            const unsigned m = __ldg(map + c);
+            i1 = m & 255u;
+            i2 = m >> 8;
+        } else {
+            i1 = LO1 + c % N1;
+            i2 = LO2 + c / N1;
+        }
         float* p = sm + i1 * ST[T1] + i2 * ST[T2];
         float* fl = nullptr;
         if (flux_g != nullptr && i1 >= NG && i1 < NG + GS && i2 >= NG && i2 < NG + GS)
@@ -268,7 +287,11 @@ __device__ __forceinline__ void prefetch_item(const SweepArgs<float>& a, int ite
     for (int v = 0; v < NV; ++v) prefetch_l2(b + v * vs, CELLS_PG * sizeof(float));
 }
 
-__device__ __forceinline__ void prolong_cell(const LevelArgs<float>& L, const ItemTab& t, int x, int y,
+// Coarse-fine ghost cell by Min-Mod interpolation.  Kept out of line: it is
+// the cold path of the gathers (coarse-fine faces only), and inlining it at
+// every gather site made the kernel's code large enough to miss in the
+// instruction cache on the hot path.
+__device__ __noinline__ void prolong_cell(const LevelArgs<float>& L, const ItemTab& t, int x, int y,
                                              int z, float val[NV]) {
     const int lp = t.par & 7;
     prolong<float>(L.uc, (size_t)L.n_groups_c * 8 * 512, t.csrc, t.cmask, lp & 1, (lp >> 1) & 1,
@@ -501,7 +524,12 @@ __device__ __forceinline__ void sweep_last_store(float* sm, float lam, float g, 
     constexpr int ST[3] = {1, XP, PD * XP};
     constexpr int S = ST[AX];
     const int c = threadIdx.x;               // < 256
-    const int i1 = NG + c % GS, i2 = NG + c / GS;
+    int i1 = NG + c % GS, i2 = NG + c / GS;  // z-columns: natural order keeps the stores coalesced
+    if (ORDER == 1) {
+        const unsigned m = __ldg(kLaneZyxS3 + c);
+        i1 = m & 255u;
+        i2 = m >> 8;
+    }
     float* p = sm + i1 * ST[T1] + i2 * ST[T2];
     float* fl = flux_g ? flux_g + AX * (3 * NV * 256) + (i2 - NG) * GS + (i1 - NG) : nullptr;
     column<AX, S, LIM>(p, 0.25f * lam, 0.5f * lam, g, gm1, fl);
@@ -509,7 +537,7 @@ __device__ __forceinline__ void sweep_last_store(float* sm, float lam, float g, 
     DiagAcc acc;
     if (AX == 0) {
         float* o = L.u_out + cell_offset(grp, 0, i1 - NG, i2 - NG);
-#pragma unroll
+#pragma unroll 1
         for (int j = 0; j < 4; ++j) {
             float u[4][NV];
 #pragma unroll
@@ -526,7 +554,7 @@ __device__ __forceinline__ void sweep_last_store(float* sm, float lam, float g, 
         }
     } else {
         float* o = L.u_out + cell_offset(grp, i1 - NG, i2 - NG, 0);
-#pragma unroll 4
+#pragma unroll 2
         for (int z = 0; z < GS; ++z) {
             float u[NV];
 #pragma unroll
@@ -595,7 +623,7 @@ __device__ __forceinline__ void finish_launch(const SweepArgs<float>& a, float* 
 // Persistent kernel.  NT = 512 threads (16 warps), one CTA per SM.  Work
 // items (level, group) come from an atomic counter, one ahead.  Per item:
 //   sweep 1: all warps (for xyz each thread first gathers the centre of its
-//            own x-row unless set B already holds it);
+//            own x-row when yp is in [3,19); sets A and B hold the rest);
 //   sweep 2: 352 columns on warps 0..10; warps 11..15 build the next item's
 //            region tables, prefetch its interior into L2 and gather its set A;
 //   sweep 3: 256 lines on warps 0..7, each thread storing its finished line
@@ -644,7 +672,13 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> 
         int slot = 0;
         build_tab(tab[0], args, s_item[0], 0);
         __syncthreads();
-        for (int r = tid; r < PD * PD; r += NT_F32) gather_row<3>(sm, args, tab[0], r % PD, r / PD);
+        // the first item whole, except what sweep 1 loads itself (xyz: the
+        // centres of the rows with yp in [3,19))
+        for (int r = tid; r < PD * PD; r += NT_F32) {
+            const int yp = r % PD, zp = r / PD;
+            if (ORDER == 0 && yp >= NG && yp < NG + GS) gather_row<2>(sm, args, tab[0], yp, zp);
+            else gather_row<3>(sm, args, tab[0], yp, zp);
+        }
 
         for (;;) {
             __syncthreads();
