@@ -46,6 +46,9 @@ def parse():
     p.add_argument("--quick", action="store_true",
                    help="device-timed value only (no e2e, FP64, L1, CPU baseline, clocks); for profiling")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    p.add_argument("--accuracy", action="store_true",
+                   help="instead of timing: per-field L1 / max error of the FP32 path against the FP64 path "
+                        "(bit-identical to the FP64 oracle) on every workload, plus positivity and conservation")
     return p.parse_args()
 
 
@@ -420,8 +423,78 @@ def run_extras(args, B, torch, H, st, cells, dev, stream):
     return out
 
 
+# ------------------------------------------------------------ accuracy
+
+def _acc_cases(W):
+    def sod_x():
+        u, npg, bc = W.sod(0)
+        return W.single_level(u, npg, bc=bc)
+    return [
+        ("cell-wise lognormal 32^3 (64 patches)", lambda: W.single_level(*W.lognormal_cells(32)), 20),
+        ("Sod tube along x, 128x16x16, outflow ends", sod_x, 20),
+        ("smooth k^-2 fields 128^3 (4096 patches)", lambda: W.single_level(*W.smooth_grf(128, seed=1001)), 100),
+        ("3-level AMR, 4096/9000/21000 patches", lambda: W.amr_grf(), 20),
+        ("lognormal sigma 1.5, rms Mach 3, 512^3 (262144 patches)",
+         lambda: W.single_level(*W.lognormal_grf(512, seed=1003, dtype=np.float32)), 50),
+        ("4-level stress, lognormal sigma 2.5, Mach <= 20 (32768 patches)", lambda: W.amr_stress("lognormal"), 20),
+        ("4-level stress, Sedov point blast (32768 patches)", lambda: W.amr_stress("sedov"), 20),
+    ]
+
+
+def run_accuracy(args):
+    """FP64 path for K steps (dt from Eq. CFL on the device), then the FP32
+    path over the same dt sequence; errors per field relative to the
+    field's largest magnitude, the worst level reported."""
+    import torch
+    from paper_0907_3390_gb300 import binding as B
+    from paper_0907_3390_gb300 import workloads as W
+    fields = ["rho", "mx", "my", "mz", "e"]
+    res = []
+    for name, make, K in _acc_cases(W):
+        H, st = make()
+        S64 = B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP64)
+        D64 = B.DeviceHierarchy(H, st, torch.float64)
+        s0, nb0 = B.gamer_hydro_check(S64.h, D64)
+        dts = []
+        for _ in range(K):
+            B.gamer_hydro_step(S64.h, D64, CFL)
+            D64.swap()
+            dts.append(B.gamer_hydro_step_result(S64.h)[0])
+        s64, nb64 = B.gamer_hydro_check(S64.h, D64)
+        S32 = B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP32)
+        D32 = B.DeviceHierarchy(H, st, torch.float32)
+        for dt in dts:
+            B.gamer_hydro_advance_all(S32.h, D32, dt)
+            D32.swap()
+        s32, nb32 = B.gamer_hydro_check(S32.h, D32)
+        l1 = np.zeros(5)
+        mx = np.zeros(5)
+        for l in range(H.n_levels):
+            ref = D64.u[l].reshape(5, -1)
+            d = (D32.u[l].double().reshape(5, -1) - ref).abs()
+            scale = ref.abs().max(dim=1).values.clamp_min(1e-300)
+            l1 = np.maximum(l1, (d.mean(dim=1) / scale).cpu().numpy())
+            mx = np.maximum(mx, (d.max(dim=1).values / scale).cpu().numpy())
+        drift = lambda s: [float(abs(a - b) / (abs(b) + 1e-30)) for a, b in zip(s, s0)]
+        res.append({"workload": name, "patches": sum(lv.n_groups for lv in H.levels) * 8, "steps": K,
+                    "l1_rel": dict(zip(fields, l1.tolist())), "max_rel": dict(zip(fields, mx.tolist())),
+                    "n_bad_initial": int(nb0), "n_bad_fp64": int(nb64), "n_bad_fp32": int(nb32),
+                    "mass_energy_drift_fp64": [drift(s64)[0], drift(s64)[4]],
+                    "mass_energy_drift_fp32": [drift(s32)[0], drift(s32)[4]]})
+        print(json.dumps(res[-1]), file=sys.stderr, flush=True)
+        S64.close()
+        S32.close()
+        del D64, D32
+        torch.cuda.empty_cache()
+    print(json.dumps({"accuracy": res, "reference": "FP64 GPU path (bit-identical to the FP64 oracle)",
+                      "cfl": CFL, "limiter": "van Leer"}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.accuracy:
+        return run_accuracy(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None
