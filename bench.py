@@ -106,17 +106,18 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def traffic_per_cell():
-    """DRAM bytes per cell-update of the FP32 sweep kernel from the committed
-    ncu summary, if it was taken on the current kernel source."""
+def profile_per_cell(key="dram_bytes_per_cell"):
+    """Per-cell-update figure of the FP32 sweep kernel (DRAM bytes, warp
+    instructions) from the committed ncu summary, if it was taken on the
+    current kernel source."""
     path = os.path.join(ROOT, "profiles", "sweep_f32_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
-    if d.get("source_sha") != kernel_source_sha():
+    if d.get("source_sha") != kernel_source_sha() or key not in d:
         return None
-    return float(d["dram_bytes_per_cell"])
+    return float(d[key])
 
 
 class ClockSampler:
@@ -160,15 +161,16 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_oracle_rate(H, states, seconds, threads):
+def cpu_oracle_rate(H, states, seconds, threads, max_groups=None):
     """Oracle (plain FP64 C, OpenMP over patch groups) on a bounded sample of
-    the workload: sweep sets of level 0, repeated until about `seconds` of
-    CPU work.  Returns cell-updates/s, the sample description and seconds."""
+    the workload: sweep sets of level 0 (or of its first max_groups patch
+    groups), repeated until about `seconds` of CPU work.  Returns
+    cell-updates/s, the sample description and seconds."""
     import oracle
     oracle.set_threads(threads)
     O = oracle.OracleLevels(H, [np.asarray(s, dtype=np.float64) for s in states])
     dt = O.cfl_dt(GAMMA, CFL)
-    n = H.levels[0].n_groups
+    n = H.levels[0].n_groups if max_groups is None else min(max_groups, H.levels[0].n_groups)
     groups = np.arange(n)
     done, el, k = 0, 0.0, 0
     while el < seconds:
@@ -177,7 +179,8 @@ def cpu_oracle_rate(H, states, seconds, threads):
         el += time.perf_counter() - t0
         done += n
         k += 1
-    return done * 4096 / el, f"{k} sweep sets of all {n} patch groups of level 0", el
+    what = f"all {n}" if n == H.levels[0].n_groups else f"the first {n}"
+    return done * 4096 / el, f"{k} sweep sets of {what} patch groups of level 0", el
 
 
 # ------------------------------------------------------------ reference arm
@@ -307,13 +310,25 @@ def run_ours(args, rank, world, dist):
     hbm, peak_kind = measured_peaks()
     k_avg = float(np.mean(kern_ms)) / 1e3
     achieved = BYTES_PER_CELL_F32 * cells / k_avg / 1e9
-    tpc = traffic_per_cell()
+    tpc = profile_per_cell("dram_bytes_per_cell")
     res["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                        "frac": achieved / hbm, "peak_kind": f"{peak_kind} copy bandwidth",
                        "traffic": None if tpc is None else tpc * cells,
                        "kernel": "k_sweep_f32 (gather + 3 sweeps + store + fused diagnostics and end-of-step "
                                  "reduction, one persistent launch)",
                        "kernel_ms": 1e3 * k_avg, "algorithmic_bytes": BYTES_PER_CELL_F32 * cells}
+    # the bound that actually limits the kernel: instruction issue (FP32
+    # arithmetic of the scheme).  Peak from the unit counts and the clock:
+    # SMs x 4 warp schedulers x 1 warp instruction per cycle x max SM clock.
+    ipc = profile_per_cell("warp_instructions_per_cell")
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    issue_peak = sms * 4 * mhz * 1e6 / 1e12
+    res["roofline_alu"] = None if ipc is None else {
+        "bound": "alu", "achieved": ipc * cells / k_avg / 1e12, "peak": issue_peak, "unit": "T warp-instr/s",
+        "frac": ipc * cells / k_avg / 1e12 / issue_peak,
+        "peak_kind": f"derived: {sms} SMs x 4 schedulers x 1 warp-instr/cycle x {mhz:.0f} MHz",
+        "instructions_per_cell": ipc}
     res["clocks"] = clk
     res["conservation_drift_rel"] = float(np.max(np.abs(sums - s0) / (np.abs(s0) + 1e-30)))
     res["n_bad"] = n_bad
@@ -418,8 +433,9 @@ def run_extras(args, B, torch, H, st, cells, dev, stream):
     # ---- the oracle on the host cores, bounded sample
     threads = os.cpu_count() or 1
     rate, sample, secs = cpu_oracle_rate(H, st, args.cpu_seconds, threads)
+    rate1, sample1, secs1 = cpu_oracle_rate(H, st, max(1.0, args.cpu_seconds / 4), 1, max_groups=16)
     out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
-                           "seconds": secs}
+                           "seconds": secs, "value_1core": rate1, "sample_1core": sample1}
     return out
 
 
@@ -522,6 +538,7 @@ def main():
                        "l2": "flushed before every timed step (256 MiB write, outside the timed interval)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "roofline": res["roofline"],
+            "roofline_alu": res["roofline_alu"],
             "gpu_launches": res["launches_per_step"] * steps,
             "clocks": res["clocks"],
             "n_bad_cells": res["n_bad"],
