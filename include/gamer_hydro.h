@@ -169,10 +169,26 @@ int gamer_hydro_advance_all(gamer_hydro_t h, const gamer_hierarchy_t *H, double 
  * gamer_hydro_step_result. */
 int gamer_hydro_step(gamer_hydro_t h, const gamer_hierarchy_t *H, double cfl);
 
-/* Result of the last gamer_hydro_step: the dt it used, the dt the next
- * step will use, the leaf sums of u * dh^3 and the bad-cell count of the
- * new state.  Waits for that step.  Any output pointer may be NULL.
- * GAMER_ERR_STATE if no step has completed. */
+/* A forward and a backward sweep set with one dt (Sec. 2.2): the xyz set
+ * and then the zyx set, each as in gamer_hydro_step, the new state back in
+ * u (u_out is scratch; the caller does NOT swap).  Every level must be at
+ * parity 0 (an xyz set next, else GAMER_ERR_STATE) and is at parity 0
+ * again afterwards.  dt comes from the device as in gamer_hydro_step and
+ * is taken new from Eq. CFL after the pair.  For a single-level FP32
+ * hierarchy the pair is ONE persistent launch: a group's zyx set starts as
+ * soon as the xyz results of the group and of its 26 neighbours are
+ * published, so the two sets overlap and share one start-up and one tail;
+ * waits are bounded (about a second), and a wait that gave up makes
+ * gamer_hydro_step_result return GAMER_ERR_TIMEOUT.  Other hierarchies run
+ * the two sets as two steps.  Captured as a CUDA graph like
+ * gamer_hydro_step.  Asynchronous; results via gamer_hydro_step_result. */
+int gamer_hydro_step_pair(gamer_hydro_t h, const gamer_hierarchy_t *H, double cfl);
+
+/* Result of the last gamer_hydro_step or gamer_hydro_step_pair: the dt it
+ * used, the dt the next step will use, the leaf sums of u * dh^3 and the
+ * bad-cell count of the new state.  Waits for that step.  Any output
+ * pointer may be NULL.  GAMER_ERR_STATE if no step has completed,
+ * GAMER_ERR_TIMEOUT if a dependency wait of a pair launch gave up. */
 int gamer_hydro_step_result(gamer_hydro_t h, double *dt_used, double *dt_next, double sums[5],
                             int64_t *n_bad);
 

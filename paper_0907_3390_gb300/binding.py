@@ -25,7 +25,8 @@ EXPORTS = [
     "gamer_hydro_create", "gamer_hydro_destroy", "gamer_hydro_set_stream",
     "gamer_hydro_set_parity", "gamer_hydro_get_parity", "gamer_hydro_cfl_dt",
     "gamer_hydro_advance", "gamer_hydro_fixup", "gamer_hydro_advance_all",
-    "gamer_hydro_check", "gamer_hydro_diagnose", "gamer_hydro_step", "gamer_hydro_step_result",
+    "gamer_hydro_check", "gamer_hydro_diagnose", "gamer_hydro_step", "gamer_hydro_step_pair",
+    "gamer_hydro_step_result",
     "gamer_hydro_diagnose_noalloc", "gamer_hydro_tune", "gamer_hydro_get_config",
     "gamer_hydro_set_profiling", "gamer_hydro_last_error",
 ]
@@ -80,6 +81,7 @@ def load(build_if_needed: bool = True) -> C.CDLL:
         L.gamer_hydro_check.argtypes = [H, hp, dp, C.POINTER(C.c_int64)]
         L.gamer_hydro_diagnose.argtypes = [H, hp, C.c_double, dp, dp, C.POINTER(C.c_int64)]
         L.gamer_hydro_step.argtypes = [H, hp, C.c_double]
+        L.gamer_hydro_step_pair.argtypes = [H, hp, C.c_double]
         L.gamer_hydro_step_result.argtypes = [H, dp, dp, dp, C.POINTER(C.c_int64)]
         L.gamer_hydro_diagnose_noalloc.argtypes = [C.c_double, C.c_int, hp, C.c_double, vp, dp, dp,
                                                    C.POINTER(C.c_int64)]
@@ -165,6 +167,11 @@ def gamer_hydro_diagnose(h, H, cfl: float):
 
 def gamer_hydro_step(h, H, cfl: float) -> None:
     _check(h, load().gamer_hydro_step(h, H.struct(), cfl))
+
+
+def gamer_hydro_step_pair(h, H, cfl: float) -> None:
+    """xyz + zyx sweep sets with one dt; the result is back in H.u (no swap)."""
+    _check(h, load().gamer_hydro_step_pair(h, H.struct(), cfl))
 
 
 def gamer_hydro_step_result(h):

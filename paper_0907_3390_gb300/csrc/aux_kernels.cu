@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(NT_FIN) k_step_final(const LevelMeta m, const 
     __shared__ double s_sum[NV * NT_FIN];
     __shared__ unsigned long long s_max[NT_FIN];
     __shared__ long long s_bad[NT_FIN];
-    step_reduce(m, pg_max, pg_sum, pg_bad, cfl, dt, update_dt, out, out_host, s_sum, s_max, s_bad);
+    step_reduce(m, pg_max, pg_sum, pg_bad, cfl, dt, update_dt, out, out_host, nullptr, s_sum, s_max, s_bad);
 }
 
 cudaError_t launch_step_final(const DiagArgs<float>& a32, const DiagArgs<double>& a64, bool fp64,

@@ -57,6 +57,19 @@ struct StepSink {
     double cfl;
     double dh;
     int update_dt;
+    int n_items;        // per-group diagnostic entries to combine
+};
+
+// An xyz set followed by a zyx set of one level in one launch (same dt).
+// Work items [0, n) are the xyz set of group i (u -> u_out); items [n, 2n)
+// the zyx set of group order1[i - n] (u_out -> u), which starts once the
+// xyz results of that group and of its 26 neighbours are published:
+// ready[g] == *epoch + 1.  ready == nullptr turns it off.
+struct PairArgs {
+    unsigned* ready;    // [n] per-group publication marks
+    unsigned* epoch;    // launch counter; the last CTA advances it
+    unsigned* status;   // nonzero after a wait gave up (reported, then cleared)
+    const int* order1;  // [n] zyx work order
 };
 
 template <typename T>
@@ -70,6 +83,7 @@ struct SweepArgs {
     const double* dt;   // device slot holding the time step
     DiagSink diag;      // fused diagnostics of the new state, or all null
     StepSink step;      // fused end-of-step reduction (needs diag), or all null
+    PairArgs pair;      // xyz + zyx pair launch, or all null
     T gamma;
     T gm1;              // gamma - 1, formed once on the host in FP64
 };

@@ -57,7 +57,10 @@ struct gamer_hydro_s {
     int total_groups = 0;
 
     // scratch
-    int* d_queue = nullptr;
+    int* d_queue = nullptr;       // [4]: work queue, finished CTAs, pair launch counter, pair status
+    unsigned* d_ready = nullptr;  // [pair_n] publication marks of pair launches
+    int* d_order1 = nullptr;      // [pair_n] zyx work order of pair launches
+    int pair_n = 0;
     unsigned long long* d_pg_max = nullptr;
     double* d_pg_sum = nullptr;
     int* d_pg_bad = nullptr;
@@ -312,6 +315,52 @@ int prepare(gamer_hydro_t h, const gamer_hierarchy_t* H) {
             }
         }
     }
+    // A pair launch writes a group's zyx result over its input once the xyz
+    // sets of the group's 26 neighbours are done, which covers every reader
+    // of that input only if the neighbour relation is symmetric.
+    bool symmetric = n == 1;
+    for (int g = 0; symmetric && g < total; ++g)
+        for (int d = 0; d < 26 && symmetric; ++d) {
+            const int q = nbr[0][(size_t)g * 26 + d];
+            const int dd = d < 13 ? d : d + 1;               // 27-cell index of direction d
+            const int opp = 26 - dd;                          // the opposite direction
+            if (q >= 0 && nbr[0][(size_t)q * 26 + (opp < 13 ? opp : opp - 1)] != g) symmetric = false;
+        }
+    if (!symmetric && h->pair_n) {
+        cudaFree(h->d_ready);
+        cudaFree(h->d_order1);
+        h->d_ready = nullptr;
+        h->d_order1 = nullptr;
+        h->pair_n = 0;
+    }
+    if (n == 1 && symmetric && h->precision == GAMER_FP32 && total > 0) {
+        // zyx work order of pair launches: a group's zyx set needs the xyz
+        // results of the group and of its 26 neighbours, and xyz items are
+        // taken in index order, so the zyx items go by the last of those
+        // indices (ties by group)
+        const int ng = total;
+        std::vector<std::pair<int, int>> key(ng);
+        for (int g = 0; g < ng; ++g) {
+            int k = g;
+            for (int d = 0; d < 26; ++d) k = std::max(k, nbr[0][(size_t)g * 26 + d]);
+            key[g] = {k, g};
+        }
+        std::sort(key.begin(), key.end());
+        std::vector<int> order(ng);
+        for (int i = 0; i < ng; ++i) order[i] = key[i].second;
+        if (h->pair_n != ng) {
+            cudaFree(h->d_ready);
+            cudaFree(h->d_order1);
+            h->d_ready = nullptr;
+            h->d_order1 = nullptr;
+            h->pair_n = 0;
+            CK(h, cudaMalloc(&h->d_ready, sizeof(unsigned) * ng));
+            CK(h, cudaMemset(h->d_ready, 0, sizeof(unsigned) * ng));   // below every launch's mark
+            CK(h, cudaMalloc(&h->d_order1, sizeof(int) * ng));
+            h->pair_n = ng;
+        }
+        CK(h, cudaMemcpy(h->d_order1, order.data(), sizeof(int) * ng, cudaMemcpyHostToDevice));
+    }
     h->n_levels = n;
     h->total_groups = total;
     h->version = H->version;
@@ -529,7 +578,7 @@ int enqueue_step(gamer_hydro_t h, const gamer_hierarchy_t* H, cudaStream_t st, b
         // the next step is an xyz step exactly when this one is zyx
         reduced = fused && item > 0;
         if (reduced)
-            a.step = StepSink{h->d_step, h->h_step_dev, h->d_dt, cfl, H->levels[0].dh, order == 1};
+            a.step = StepSink{h->d_step, h->h_step_dev, h->d_dt, cfl, H->levels[0].dh, order == 1, item};
         if (item > 0) {
             cudaError_t e = cudaSuccess;
             if (h->prof_ev[0]) e = cudaEventRecord(h->prof_ev[0], st);
@@ -576,6 +625,64 @@ int enqueue_step(gamer_hydro_t h, const gamer_hierarchy_t* H, cudaStream_t st, b
     return r;
 }
 
+// The hierarchy with u and u_out exchanged on every level (the second set
+// of a pair when it runs as two steps).
+struct SwappedHierarchy {
+    gamer_level_t lv[MAXLEV];
+    gamer_hierarchy_t H;
+    explicit SwappedHierarchy(const gamer_hierarchy_t* src) {
+        for (int l = 0; l < src->n_levels; ++l) {
+            lv[l] = src->levels[l];
+            lv[l].u = src->levels[l].u_out;
+            lv[l].u_out = const_cast<void*>(src->levels[l].u);
+        }
+        H = *src;
+        H.levels = lv;
+    }
+};
+
+// Launch sequence of one sweep-set pair (xyz then zyx, same dt) on stream
+// st, the result back in u.  One level in FP32: a single pair launch whose
+// last CTA also reduces the diagnostics and writes dt and the step result.
+// Otherwise: two whole steps, the second on the swapped hierarchy.
+int enqueue_pair(gamer_hydro_t h, const gamer_hierarchy_t* H, cudaStream_t st, double cfl) {
+    const int n = H->levels[0].n_groups;
+    if (!(h->precision == GAMER_FP32 && H->n_levels == 1 && n > 0 && h->pair_n == n)) {
+        int r = enqueue_step(h, H, st, true, cfl);
+        if (r) return r;
+        for (int l = 0; l < H->n_levels; ++l) h->parity[l] ^= 1;
+        SwappedHierarchy S(H);
+        r = enqueue_step(h, &S.H, st, true, cfl);
+        for (int l = 0; l < H->n_levels; ++l) h->parity[l] ^= 1;
+        return r;
+    }
+    SweepArgs<float> a;
+    memset(&a, 0, sizeof(a));
+    fill_level<float>(a.lv[0], H->levels, 0, h);
+    SwappedHierarchy S(H);
+    fill_level<float>(a.lv[1], S.H.levels, 0, h);
+    a.lv[0].item0 = 0;
+    a.lv[1].item0 = n;
+    a.n_levels = 2;
+    a.total = 2 * n;
+    a.queue = h->d_queue;
+    a.done = reinterpret_cast<unsigned*>(h->d_queue + 1);
+    a.dt = h->d_dt;
+    a.gamma = (float)h->gamma;
+    a.gm1 = (float)(h->gamma - 1.0);
+    a.diag = DiagSink{h->d_pg_max, h->d_pg_sum, h->d_pg_bad};
+    // after a zyx set the next set is an xyz set: take the new dt
+    a.step = StepSink{h->d_step, h->h_step_dev, h->d_dt, cfl, H->levels[0].dh, 1, n};
+    a.pair = PairArgs{h->d_ready, reinterpret_cast<unsigned*>(h->d_queue + 2),
+                      reinterpret_cast<unsigned*>(h->d_queue + 3), h->d_order1};
+    cudaError_t e = cudaSuccess;
+    if (h->prof_ev[0]) e = cudaEventRecord(h->prof_ev[0], st);
+    if (e == cudaSuccess) e = launch_sweep_pair(a, h->limiter, std::max(1, std::min(2 * n, h->sm_count)), st);
+    if (e == cudaSuccess && h->prof_ev[1]) e = cudaEventRecord(h->prof_ev[1], st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "FP32 pair launch");
+    return GAMER_OK;
+}
+
 // dt of the current state (Eq. CFL) into h->d_dt, on the handle's stream.
 int diagnose_to_device(gamer_hydro_t h, const gamer_hierarchy_t* H, double cfl) {
     DiagArgs<float> d32;
@@ -616,9 +723,10 @@ int gamer_hydro_create(double gamma, int limiter, int ghost_width, int precision
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
     // work-queue counter and finished-CTA counter: zeroed once here, set back
-    // to zero by the last CTA of every FP32 sweep launch
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_queue, 2 * sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(h->d_queue, 0, 2 * sizeof(int));
+    // to zero by the last CTA of every FP32 sweep launch; then the pair
+    // launch counter and the pair wait-status word
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_queue, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->d_queue, 0, 4 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_dt, sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_step, sizeof(StepOut));
     if (e == cudaSuccess) e = cudaMemset(h->d_step, 0, sizeof(StepOut));
@@ -648,6 +756,8 @@ int gamer_hydro_destroy(gamer_hydro_t h) {
     else cudaDeviceSynchronize();
     drop_hierarchy(h);
     cudaFree(h->d_queue);
+    cudaFree(h->d_ready);
+    cudaFree(h->d_order1);
     cudaFree(h->d_dt);
     cudaFree(h->d_pg_max);
     cudaFree(h->d_pg_sum);
@@ -810,6 +920,57 @@ int gamer_hydro_step(gamer_hydro_t h, const gamer_hierarchy_t* H, double cfl) {
     return GAMER_OK;
 }
 
+int gamer_hydro_step_pair(gamer_hydro_t h, const gamer_hierarchy_t* H, double cfl) {
+    if (!h) return GAMER_ERR_ARG;
+    if (!(cfl > 0.0) || !std::isfinite(cfl)) return fail(h, GAMER_ERR_ARG, "cfl must be positive");
+    CK(h, cudaSetDevice(h->device));
+    int r = prepare(h, H);
+    if (r) return r;
+    if ((r = check_pointers(h, H, true))) return r;
+    if ((r = check_same_parity(h, H))) return r;
+    if (h->parity[0] != 0) return fail(h, GAMER_ERR_STATE, "a sweep-set pair starts with an xyz set (parity 0)");
+    if (!h->dt_ready || h->dt_version != h->version) {
+        if ((r = diagnose_to_device(h, H, cfl))) return r;
+        h->dt_ready = true;
+        h->dt_version = h->version;
+    }
+    if (h->prof_ev[0]) {
+        if ((r = enqueue_pair(h, H, h->stream, cfl))) return r;
+        CK(h, cudaEventRecord(h->step_event, h->stream));
+        return GAMER_OK;
+    }
+    char key[64];
+    snprintf(key, sizeof(key), "pair|%llu|%.17g|", (unsigned long long)h->version, cfl);
+    std::string k = key;
+    for (int l = 0; l < H->n_levels; ++l) {
+        snprintf(key, sizeof(key), "%p,%p,%p;", H->levels[l].u, H->levels[l].u_out, H->levels[l].face_flux);
+        k += key;
+    }
+    auto it = h->graphs.find(k);
+    if (it == h->graphs.end()) {
+        if (!h->cap_stream) CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        if (h->graphs.size() >= 16) drop_graphs(h);
+        cudaGraph_t graph = nullptr;
+        CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        r = enqueue_pair(h, H, h->cap_stream, cfl);
+        cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (r) {
+            if (graph) cudaGraphDestroy(graph);
+            return r;
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+        GraphEntry ge;
+        e = cudaGraphInstantiate(&ge.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+        it = h->graphs.emplace(k, ge).first;
+    }
+    it->second.last_use = ++h->use_clock;
+    CK(h, cudaGraphLaunch(it->second.exec, h->stream));
+    CK(h, cudaEventRecord(h->step_event, h->stream));
+    return GAMER_OK;
+}
+
 int gamer_hydro_step_result(gamer_hydro_t h, double* dt_used, double* dt_next, double sums[5],
                             int64_t* n_bad) {
     if (!h) return GAMER_ERR_ARG;
@@ -817,6 +978,8 @@ int gamer_hydro_step_result(gamer_hydro_t h, double* dt_used, double* dt_next, d
     CK(h, cudaEventSynchronize(h->step_event));
     const StepOut& o = *h->h_step;
     if (o.steps == 0) return fail(h, GAMER_ERR_STATE, "no step has completed on this handle");
+    if (o.status != 0)
+        return fail(h, GAMER_ERR_TIMEOUT, "a dependency wait of the last pair launch gave up; its result is invalid");
     if (dt_used) *dt_used = o.dt_used;
     if (dt_next) *dt_next = o.dt_next;
     if (sums)

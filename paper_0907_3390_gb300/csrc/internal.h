@@ -16,6 +16,8 @@ namespace gh {
 cudaError_t launch_sweep_f32(const SweepArgs<float>& a, int order, int lim, int variant, int threads, int grid,
                              cudaStream_t st);
 size_t sweep_f32_smem();
+// xyz + zyx pair of one level (a.pair set, a.total = 2 n, lv[1] = lv[0] with u / u_out swapped)
+cudaError_t launch_sweep_pair(const SweepArgs<float>& a, int lim, int grid, cudaStream_t st);
 cudaError_t sweep_f32_init();
 // threads per block: 128 or 256
 cudaError_t launch_pg_f64(const LevelArgs<double>& L, int g0, int count, int order, int lim,

@@ -21,6 +21,7 @@ struct StepOut {
     double sum[NV];     // leaf sums of u * dh^3
     long long n_bad;
     long long steps;
+    long long status;   // nonzero: a dependency wait of the step gave up
 };
 
 struct LevelMeta {
@@ -35,14 +36,15 @@ struct LevelMeta {
 // s_max [NT_FIN], s_bad [NT_FIN] in shared memory.  The per-group inputs are
 // read through L2 (they may have been written by other CTAs of the same
 // launch).  The result goes to *out and, when out_host is given, to that
-// mapped host copy as well (no copy node needed after the kernel).  *dt becomes the new value when update_dt is set (the next step
+// mapped host copy as well (no copy node needed after the kernel).  status:
+// the launch's wait-failure word, copied into the result and cleared.  *dt becomes the new value when update_dt is set (the next step
 // is an xyz step), otherwise it is held (one dt for a forward and backward
 // sweep set, Sec. 2.2).  Products are rounded explicitly so that the result
 // is the same under any contraction setting of the including file.
 __device__ __forceinline__ void step_reduce(const LevelMeta& m, const unsigned long long* pg_max,
                                             const double* pg_sum, const int* pg_bad, double cfl, double* dt,
-                                            int update_dt, StepOut* out, StepOut* out_host, double* s_sum,
-                                            unsigned long long* s_max, long long* s_bad) {
+                                            int update_dt, StepOut* out, StepOut* out_host, unsigned* status,
+                                            double* s_sum, unsigned long long* s_max, long long* s_bad) {
     const int t = threadIdx.x;
     const bool act = t < NT_FIN;
     double tot[NV] = {0, 0, 0, 0, 0};
@@ -97,6 +99,11 @@ __device__ __forceinline__ void step_reduce(const LevelMeta& m, const unsigned l
         for (int v = 0; v < NV; ++v) o.sum[v] = tot[v];
         o.n_bad = nb;
         o.steps = out->steps + 1;
+        o.status = 0;
+        if (status != nullptr) {
+            o.status = *status;
+            *status = 0u;
+        }
         *out = o;
         if (out_host != nullptr) *out_host = o;
         if (update_dt) *dt = dnew;

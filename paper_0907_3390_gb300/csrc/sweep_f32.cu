@@ -264,7 +264,8 @@ __device__ __forceinline__ int level_of(const SweepArgs<float>& a, int item) {
 __device__ __forceinline__ void build_tab(ItemTab& t, const SweepArgs<float>& a, int item, int t0) {
     const int l = level_of(a, item);
     const LevelArgs<float>& L = a.lv[l];
-    const int g = item - L.item0;
+    int g = item - L.item0;
+    if (a.pair.ready != nullptr && l == 1) g = a.pair.order1[g];   // zyx half of a pair launch
     const int tid = (int)threadIdx.x - t0;
     if (tid >= 0 && tid < 27) region_entry(L.nbr, g, tid, t.src, t.mask);
     if (tid >= 32 && tid < 59 && L.parent != nullptr)
@@ -280,9 +281,12 @@ __device__ __forceinline__ void build_tab(ItemTab& t, const SweepArgs<float>& a,
 
 // The interior of a work item into L2 (5 contiguous 16 KiB runs).
 __device__ __forceinline__ void prefetch_item(const SweepArgs<float>& a, int item) {
-    const LevelArgs<float>& L = a.lv[level_of(a, item)];
+    const int l = level_of(a, item);
+    const LevelArgs<float>& L = a.lv[l];
+    int g = item - L.item0;
+    if (a.pair.ready != nullptr && l == 1) g = a.pair.order1[g];
     const size_t vs = (size_t)L.n_groups * 8 * 512;
-    const float* b = L.u + ((size_t)(item - L.item0) << 12);
+    const float* b = L.u + ((size_t)g << 12);
 #pragma unroll
     for (int v = 0; v < NV; ++v) prefetch_l2(b + v * vs, CELLS_PG * sizeof(float));
 }
@@ -606,18 +610,19 @@ __device__ __forceinline__ void finish_launch(const SweepArgs<float>& a, float* 
     if (threadIdx.x == 0) {
         *a.queue = 0;
         *a.done = 0u;
+        if (a.pair.epoch != nullptr) *a.pair.epoch += 1u;   // every CTA read it before counting out
     }
     if (a.step.out == nullptr) return;
     LevelMeta m;
     m.n_levels = 1;
     m.item0[0] = 0;
-    m.n[0] = a.total;
+    m.n[0] = a.step.n_items;
     m.dh[0] = a.step.dh;
     double* s_sum = reinterpret_cast<double*>(sm);
     unsigned long long* s_max = reinterpret_cast<unsigned long long*>(s_sum + NV * NT_FIN);
     long long* s_bad = reinterpret_cast<long long*>(s_max + NT_FIN);
     step_reduce(m, a.diag.pg_max, a.diag.pg_sum, a.diag.pg_bad, a.step.cfl, a.step.dt, a.step.update_dt,
-                a.step.out, a.step.out_host, s_sum, s_max, s_bad);
+                a.step.out, a.step.out_host, a.pair.status, s_sum, s_max, s_bad);
 }
 
 // Persistent kernel.  NT = 512 threads (16 warps), one CTA per SM.  Work
@@ -729,6 +734,182 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> 
     finish_launch(args, sm, &s_cnt[2]);
 }
 
+// ---------------------------------------------------------------- pair launch
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Warp-collective: are the xyz results of group g and of its 26 neighbours
+// published in this launch?
+__device__ __forceinline__ bool inputs_ready(const SweepArgs<float>& a, int g, unsigned target) {
+    const int lane = threadIdx.x & 31;
+    int n = -1;
+    if (lane < 26) n = a.lv[0].nbr[(size_t)g * 26 + lane];
+    else if (lane == 26) n = g;
+    const bool ok = n < 0 || ld_acquire_u32(a.pair.ready + n) == target;
+    return __all_sync(0xffffffffu, ok);
+}
+
+// Warp-collective wait for inputs_ready, bounded (about a second): a wait
+// that runs out sets the launch's status word and goes on, and the step
+// reports a timeout instead of hanging.
+constexpr unsigned PAIR_SPIN_LIMIT = 1u << 21;
+__device__ __forceinline__ void wait_inputs(const SweepArgs<float>& a, int g, unsigned target) {
+    for (unsigned it = 0;; ++it) {
+        if (inputs_ready(a, g, target)) break;
+        if (ld_acquire_u32(a.pair.status) != 0u) break;    // an earlier wait gave up: do not wait again
+        if (it >= PAIR_SPIN_LIMIT) {
+            if ((threadIdx.x & 31) == 0) atomicOr(a.pair.status, 1u);
+            break;
+        }
+        __nanosleep(256);
+    }
+    __threadfence();
+}
+
+// Publish the xyz result of group g.  Its stores were made by other threads
+// of the block before a block-wide barrier that precedes this call; the
+// fence orders them (cumulatively) before the mark.
+__device__ __forceinline__ void publish(const SweepArgs<float>& a, int g, unsigned target) {
+    __threadfence();
+    st_release_u32(a.pair.ready + g, target);
+}
+
+// Pair launch: the xyz set and then the zyx set of one level with the same
+// dt (the forward and backward sweep of Sec. 2.2), u -> u_out -> u, in one
+// persistent launch.  Items follow the pipelined kernel above, with the
+// order taken per item.  A zyx item reads the xyz results of its group and
+// of the 26 neighbours, so it starts only once those are published; its
+// ghost slabs are gathered alongside the previous item when that item is
+// also a zyx item and the inputs are already published, otherwise after it
+// (the CTA first publishes its own pending xyz result, so no CTA ever waits
+// on itself).  Waits are only for items already claimed by running CTAs,
+// and xyz items never wait, so the launch always completes.
+template <int LIM>
+__global__ void __launch_bounds__(NT_F32, 1) k_sweep_pair(const SweepArgs<float> args) {
+    extern __shared__ float sm[];
+    ItemTab* tab = reinterpret_cast<ItemTab*>(sm + NV * VS);     // [2]
+    int* s_item = reinterpret_cast<int*>(tab + 2);               // current, next (queue indices)
+    int* s_cnt = s_item + 2;          // gather-set counters A, B; last-CTA flag; next item deferred
+    float* s_red = reinterpret_cast<float*>(s_cnt + 4);          // [8 warps][12]
+    int* s_aux = reinterpret_cast<int*>(s_red + 8 * 12);         // pending publication, target mark
+    const int tid = threadIdx.x;
+    const int total = args.total;
+    const bool diag = args.diag.pg_max != nullptr;
+
+    if (tid == 0) {
+        s_item[0] = atomicAdd(args.queue, 1);
+        s_item[1] = atomicAdd(args.queue, 1);
+        s_cnt[0] = s_cnt[1] = 0;
+        s_aux[0] = -1;
+        s_aux[1] = (int)(ld_acquire_u32(args.pair.epoch) + 1u);
+    }
+    __syncthreads();
+    const unsigned target = (unsigned)s_aux[1];
+    do {
+        if (s_item[0] >= total) break;
+        int slot = 0;
+        build_tab(tab[0], args, s_item[0], 0);
+        __syncthreads();
+        if (tab[0].level == 0) {
+            for (int r = tid; r < PD * PD; r += NT_F32) {
+                const int yp = r % PD, zp = r / PD;
+                if (yp >= NG && yp < NG + GS) gather_row<2>(sm, args, tab[0], yp, zp);
+                else gather_row<3>(sm, args, tab[0], yp, zp);
+            }
+        } else {
+            if (tid < 32) wait_inputs(args, tab[0].g, target);
+            __syncthreads();
+            for (int r = tid; r < PD * PD; r += NT_F32) gather_row<3>(sm, args, tab[0], r % PD, r / PD);
+        }
+
+        for (;;) {
+            __syncthreads();
+            const int next = s_item[1];
+            const bool has_next = next < total;
+            const ItemTab& cur = tab[slot];
+            ItemTab& nxt = tab[slot ^ 1];
+            const int ord = cur.level;                       // 0: xyz, 1: zyx
+            const LevelArgs<float>& L = args.lv[ord];
+            const float lam = cur.lam;
+            const int cur_g = cur.g;
+
+            if (ord == 0) sweep_first<0, LIM>(sm, args, cur, lam, nullptr);
+            else sweep_first<1, LIM>(sm, args, cur, lam, nullptr);
+            __syncthreads();
+            if (tid == 11 * 32 && s_aux[0] >= 0) {
+                publish(args, s_aux[0], target);       // the previous xyz item
+                s_aux[0] = -1;
+            }
+            if (tid < 11 * 32) {
+                if (ord == 0) sweep<0, 1, LIM>(sm, lam, args.gamma, args.gm1, nullptr, 11 * 32);
+                else sweep<1, 1, LIM>(sm, lam, args.gamma, args.gm1, nullptr, 11 * 32);
+            } else if (has_next) {
+                build_tab(nxt, args, next, 11 * 32);
+                if (tid == 11 * 32) prefetch_item(args, next);
+                asm volatile("bar.sync 1, 160;" ::: "memory");      // warps 11..15: tables ready
+                if (tid < 12 * 32) {
+                    bool go = nxt.level == ord;
+                    if (go && ord == 1) go = inputs_ready(args, nxt.g, target);
+                    if (tid == 11 * 32) s_cnt[3] = go ? 0 : 1;
+                }
+                asm volatile("bar.sync 1, 160;" ::: "memory");
+                if (s_cnt[3] == 0) {
+                    if (ord == 0) gather_pool<0, 0>(sm, args, nxt, &s_cnt[0]);
+                    else gather_pool<1, 0>(sm, args, nxt, &s_cnt[0]);
+                }
+            }
+            __syncthreads();
+            if (tid < 8 * 32) {
+                if (ord == 0) sweep_last_store<0, LIM>(sm, lam, args.gamma, args.gm1, nullptr, L, cur_g, false, s_red);
+                else sweep_last_store<1, LIM>(sm, lam, args.gamma, args.gm1, nullptr, L, cur_g, diag, s_red);
+                if (tid == 0) {
+                    s_item[0] = next;
+                    s_item[1] = has_next ? atomicAdd(args.queue, 1) : next;
+                }
+            } else if (has_next && s_cnt[3] == 0) {
+                if (ord == 0) gather_pool<0, 1>(sm, args, nxt, &s_cnt[1]);
+                else gather_pool<1, 1>(sm, args, nxt, &s_cnt[1]);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                s_cnt[0] = s_cnt[1] = 0;
+                if (ord == 0) s_aux[0] = cur_g;       // published in the next phase 2, or below
+            }
+            if (ord == 1 && diag) finish_diag(args.diag, cur_g, s_red, 8);
+            if (!has_next) break;
+            slot ^= 1;
+            if (s_cnt[3] != 0) {
+                // a zyx item not gathered alongside: publish our own pending xyz
+                // result (the item may need it), wait for its inputs, gather it
+                __syncthreads();
+                if (tid == 0 && s_aux[0] >= 0) {
+                    publish(args, s_aux[0], target);
+                    s_aux[0] = -1;
+                }
+                if (tid < 32) wait_inputs(args, tab[slot].g, target);
+                __syncthreads();
+                for (int r = tid; r < PD * PD; r += NT_F32) gather_row<3>(sm, args, tab[slot], r % PD, r / PD);
+            } else if (ord == 1) {
+                for (int r = tid; r < GS * GS + 2 * GS * GS; r += NT_F32) {
+                    if (r < GS * GS) gather_row<2>(sm, args, tab[slot], NG + r % GS, NG + r / GS);
+                    else gather_task<1, 3>(sm, args, tab[slot], r - GS * GS);
+                }
+            }
+        }
+    } while (false);
+    __syncthreads();
+    if (tid == 0 && s_aux[0] >= 0) publish(args, s_aux[0], target);
+    finish_launch(args, sm, &s_cnt[2]);
+}
+
 // Non-pipelined variant (an autotuner candidate): per item, all NT threads
 // gather the whole padded block, then the three sweeps run with every
 // thread, the last one storing its lines; the next item's interior is
@@ -791,7 +972,7 @@ cudaError_t sweep_f32_init() {
         set_attr(k_sweep_f32_simple<0, 1, 256>), set_attr(k_sweep_f32_simple<1, 0, 256>),
         set_attr(k_sweep_f32_simple<1, 1, 256>), set_attr(k_sweep_f32_simple<0, 0, 512>),
         set_attr(k_sweep_f32_simple<0, 1, 512>), set_attr(k_sweep_f32_simple<1, 0, 512>),
-        set_attr(k_sweep_f32_simple<1, 1, 512>)};
+        set_attr(k_sweep_f32_simple<1, 1, 512>), set_attr(k_sweep_pair<0>), set_attr(k_sweep_pair<1>)};
     for (cudaError_t x : r)
         if (x != cudaSuccess) e = x;
     return e;
@@ -818,6 +999,12 @@ static cudaError_t launch_variant(const SweepArgs<float>& a, int variant, int th
 }
 
 size_t sweep_f32_smem() { return SMEM_F32; }
+
+cudaError_t launch_sweep_pair(const SweepArgs<float>& a, int lim, int grid, cudaStream_t st) {
+    if (lim == 0) k_sweep_pair<0><<<grid, NT_F32, SMEM_F32, st>>>(a);
+    else k_sweep_pair<1><<<grid, NT_F32, SMEM_F32, st>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_sweep_f32(const SweepArgs<float>& a, int order, int lim, int variant, int threads, int grid,
                              cudaStream_t st) {

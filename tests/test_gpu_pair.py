@@ -1,0 +1,123 @@
+"""The sweep-set pair (gamer_hydro_step_pair): an xyz and a zyx set with one
+dt (Sec. 2.2), the result back in u.  For one FP32 level it is a single
+persistent launch in which a group's zyx set starts once the xyz results of
+the group and of its 26 neighbours are published; other hierarchies run it
+as two steps.  Either way it must equal two gamer_hydro_step calls bit for
+bit (states, dt sequence, sums): the same arithmetic on the same values,
+only the start times of the zyx items differ.  Group layouts: 2x2x2, 8^3,
+one self-periodic group, 37x1x1 and 5x3x3 (groups that are their own or
+each other's neighbours several times over), a Sod tube with outflow ends,
+and a three-level AMR hierarchy (two-step path)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_0907_3390_gb300 import binding as B  # noqa: E402
+from paper_0907_3390_gb300 import hierarchy as hm  # noqa: E402
+from paper_0907_3390_gb300 import workloads as wl  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+G = 5.0 / 3.0
+PREC = {"f32": (B.GAMER_FP32, torch.float32), "f64": (B.GAMER_FP64, torch.float64)}
+
+
+def random_domain(npg, seed):
+    rng = np.random.default_rng(seed)
+    shape = (16 * npg[2], 16 * npg[1], 16 * npg[0])
+    rho = np.exp(0.5 * rng.standard_normal(shape) - 0.125)
+    v = [0.3 * rng.standard_normal(shape) for _ in range(3)]
+    P = 1.0 + 0.1 * rng.random(shape)
+    return wl.single_level(wl.prim_to_cons(rho, *v, P), npg)
+
+
+def amr_small():
+    def score(level, centres):
+        x, y, z = (centres[a][:, 0, 0, 0] for a in range(3))
+        r = np.sqrt((x - 0.45) ** 2 + (y - 0.55) ** 2 + (z - 0.5) ** 2)
+        return 0.3 - r if level == 0 else 0.17 - r
+    H = hm.build_hierarchy((3, 3, 3), score, 3)
+
+    def prim(x, y, z, dh):
+        rho = 1.0 + 0.3 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+        return rho, 0.3 * np.cos(2 * np.pi * y), 0.2 * np.sin(2 * np.pi * z), -0.25 * np.cos(2 * np.pi * x), \
+            0.8 + 0.1 * np.cos(2 * np.pi * (x + y))
+    return H, wl.level_fields(H, prim)
+
+
+def sod_y():
+    u, npg, bc = wl.sod(1, 128, 16)
+    return wl.single_level(u, npg, bc=bc)
+
+
+CASES = {
+    "2x2x2": lambda: wl.single_level(*wl.lognormal_cells(32)),
+    "8^3 smooth": lambda: wl.single_level(*wl.smooth_grf(128, seed=1001)),
+    "1 group": lambda: random_domain((1, 1, 1), 11),
+    "37x1x1": lambda: random_domain((37, 1, 1), 12),
+    "5x3x3": lambda: random_domain((5, 3, 3), 13),
+    "sod y": sod_y,
+    "amr 3 levels": amr_small,
+}
+
+
+def compare(H, st, prec, n_pairs, profiled=False):
+    p, dt_ = PREC[prec]
+    S1, S2 = B.Solver(G, 0, p), B.Solver(G, 0, p)
+    D1, D2 = B.DeviceHierarchy(H, st, dt_), B.DeviceHierarchy(H, st, dt_)
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    if profiled:
+        for e in ev:
+            e.record()          # materialise the underlying cudaEvent_t
+        torch.cuda.synchronize()
+        B.gamer_hydro_set_profiling(S2.h, ev[0], ev[1])
+    for k in range(n_pairs):
+        for _ in range(2):
+            B.gamer_hydro_step(S1.h, D1, 0.5)
+            D1.swap()
+        r1 = B.gamer_hydro_step_result(S1.h)
+        B.gamer_hydro_step_pair(S2.h, D2, 0.5)
+        r2 = B.gamer_hydro_step_result(S2.h)
+        assert B.gamer_hydro_get_parity(S2.h, 0) == 0
+        assert r1[0] == r2[0] and r1[1] == r2[1], (k, r1[:2], r2[:2])
+        assert r1[3] == r2[3]
+        assert np.array_equal(r1[2], r2[2]), (k, r1[2] - r2[2])
+        for l in range(H.n_levels):
+            assert torch.equal(D1.u[l], D2.u[l]), (k, l)
+    if profiled:
+        B.gamer_hydro_set_profiling(S2.h, None, None)
+    S1.close()
+    S2.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_pair_equals_two_steps(case, prec):
+    if prec == "f64" and case == "8^3 smooth":
+        pytest.skip("the FP64 pair is the two-step path; covered by the smaller layouts")
+    H, st = CASES[case]()
+    compare(H, st, prec, 3)
+
+
+def test_pair_many_replays_and_profiled_launch():
+    # graph replays carry the launch counter on the device; the profiled
+    # path launches directly
+    H, st = CASES["8^3 smooth"]()
+    compare(H, st, "f32", 8)
+    compare(H, st, "f32", 2, profiled=True)
+
+
+def test_pair_needs_xyz_parity():
+    H, st = CASES["2x2x2"]()
+    S = B.Solver(G, 0, B.GAMER_FP32)
+    D = B.DeviceHierarchy(H, st, torch.float32)
+    B.gamer_hydro_step(S.h, D, 0.5)
+    D.swap()
+    with pytest.raises(B.GamerError) as e:
+        B.gamer_hydro_step_pair(S.h, D, 0.5)
+    assert e.value.code == B.GAMER_ERR_STATE
+    B.gamer_hydro_step(S.h, D, 0.5)
+    D.swap()
+    B.gamer_hydro_step_pair(S.h, D, 0.5)
+    assert B.gamer_hydro_step_result(S.h)[3] == 0
+    S.close()
