@@ -46,6 +46,9 @@ def parse():
     p.add_argument("--quick", action="store_true",
                    help="device-timed value only (no e2e, FP64, L1, CPU baseline, clocks); for profiling")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    p.add_argument("--mode", choices=["pair", "step"], default="pair",
+                   help="pair: one call = gamer_hydro_step_pair (xyz + zyx sweep sets with one dt, one launch); "
+                        "step: one call = gamer_hydro_step (one sweep set)")
     p.add_argument("--accuracy", action="store_true",
                    help="instead of timing: per-field L1 / max error of the FP32 path against the FP64 path "
                         "(bit-identical to the FP64 oracle) on every workload, plus positivity and conservation")
@@ -87,6 +90,16 @@ WORKLOADS = {
 }
 
 
+STEP_PAIR = ("gamer_hydro_step_pair: the xyz and the zyx sweep set of every patch group with one dt "
+             "(2 cell-updates per cell), each set = ghost gather + 3 sweeps, then the CFL dt and the "
+             "conservation/positivity check; one CUDA graph of ONE persistent kernel (a group's zyx set starts "
+             "when its and its neighbours' xyz results are published; the last CTA reduces the diagnostics and "
+             "writes dt and the result to mapped host memory)")
+STEP_ONE = ("gamer_hydro_step: one sweep set (gather + 3 sweeps) + CFL dt + conservation/positivity check "
+            "(one CUDA graph: persistent sweep kernel with fused diagnostics; its last CTA reduces them and "
+            "writes dt and the result to mapped host memory)")
+
+
 # ------------------------------------------------------------ helpers
 
 def measured_peaks():
@@ -100,17 +113,18 @@ def measured_peaks():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("sweep_f32.cu", "common.cuh", "step_reduce.cuh"):
+    for f in ("sweep_f32.cu", "common.cuh", "step_reduce.cuh", "lane_maps.h"):
         with open(os.path.join(ROOT, "paper_0907_3390_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profile_per_cell(key="dram_bytes_per_cell"):
-    """Per-cell-update figure of the FP32 sweep kernel (DRAM bytes, warp
-    instructions) from the committed ncu summary, if it was taken on the
+def profile_per_cell(key="dram_bytes_per_cell", kernel="sweep_f32"):
+    """Per-cell-update figure of an FP32 sweep kernel (DRAM bytes, warp
+    instructions; kernel 'sweep_f32' = k_sweep_f32, 'sweep_pair' =
+    k_sweep_pair) from the committed ncu summary, if it was taken on the
     current kernel source."""
-    path = os.path.join(ROOT, "profiles", "sweep_f32_traffic.json")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
@@ -254,9 +268,14 @@ def run_ours(args, rank, world, dist):
     D = B.DeviceHierarchy(H, st, torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    sets = 2 if args.mode == "pair" else 1   # sweep sets (cell-updates per cell) per call
+
     def step():
-        B.gamer_hydro_step(S.h, D, CFL)      # sweeps + CFL dt + check, one graph replay
-        D.swap()
+        if args.mode == "pair":
+            B.gamer_hydro_step_pair(S.h, D, CFL)   # xyz + zyx sets, CFL dt, check: one graph replay
+        else:
+            B.gamer_hydro_step(S.h, D, CFL)        # one sweep set, CFL dt, check: one graph replay
+            D.swap()
 
     s0, _ = B.gamer_hydro_check(S.h, D)
     clocks = None if args.quick else ClockSampler(local)
@@ -299,34 +318,38 @@ def run_ours(args, rank, world, dist):
         t_max = float(t.item())
     else:
         t_max = t_local
-    value = cells * args.steps * world / t_max
-    res = {"value": value, "ms_per_step": 1e3 * t_max / args.steps}
+    value = cells * sets * args.steps * world / t_max
+    res = {"value": value, "ms_per_step": 1e3 * t_max / args.steps, "sets_per_step": sets}
     # kernels per step: one level = the persistent sweep launch alone (it runs
     # the end-of-step reduction in its last CTA); more levels = the sweep
     # launch, one fix-up per coarse level, the diagnostics and the reduction
     n_lev = len(H.levels)
-    res["launches_per_step"] = 1 if n_lev == 1 else n_lev + 2
+    res["launches_per_step"] = 1 if n_lev == 1 else sets * (n_lev + 2)
 
     hbm, peak_kind = measured_peaks()
     k_avg = float(np.mean(kern_ms)) / 1e3
-    achieved = BYTES_PER_CELL_F32 * cells / k_avg / 1e9
-    tpc = profile_per_cell("dram_bytes_per_cell")
+    achieved = BYTES_PER_CELL_F32 * sets * cells / k_avg / 1e9
+    kname = "sweep_pair" if sets == 2 and n_lev == 1 else "sweep_f32"
+    tpc = profile_per_cell("dram_bytes_per_cell", kname)
     res["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                        "frac": achieved / hbm, "peak_kind": f"{peak_kind} copy bandwidth",
-                       "traffic": None if tpc is None else tpc * cells,
-                       "kernel": "k_sweep_f32 (gather + 3 sweeps + store + fused diagnostics and end-of-step "
-                                 "reduction, one persistent launch)",
-                       "kernel_ms": 1e3 * k_avg, "algorithmic_bytes": BYTES_PER_CELL_F32 * cells}
+                       "traffic": None if tpc is None else tpc * sets * cells,
+                       "kernel": ("k_sweep_pair (xyz and zyx sets of every group: gathers, 2 x 3 sweeps, stores, "
+                                  "fused diagnostics and end-of-step reduction, one persistent launch)"
+                                  if kname == "sweep_pair" else
+                                  "k_sweep_f32 (gather + 3 sweeps + store + fused diagnostics and end-of-step "
+                                  "reduction, one persistent launch)"),
+                       "kernel_ms": 1e3 * k_avg, "algorithmic_bytes": BYTES_PER_CELL_F32 * sets * cells}
     # the bound that actually limits the kernel: instruction issue (FP32
     # arithmetic of the scheme).  Peak from the unit counts and the clock:
     # SMs x 4 warp schedulers x 1 warp instruction per cycle x max SM clock.
-    ipc = profile_per_cell("warp_instructions_per_cell")
+    ipc = profile_per_cell("warp_instructions_per_cell", kname)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = (clk or {}).get("sm_max_mhz") or 2070.0
     issue_peak = sms * 4 * mhz * 1e6 / 1e12
     res["roofline_alu"] = None if ipc is None else {
-        "bound": "alu", "achieved": ipc * cells / k_avg / 1e12, "peak": issue_peak, "unit": "T warp-instr/s",
-        "frac": ipc * cells / k_avg / 1e12 / issue_peak,
+        "bound": "alu", "achieved": ipc * sets * cells / k_avg / 1e12, "peak": issue_peak, "unit": "T warp-instr/s",
+        "frac": ipc * sets * cells / k_avg / 1e12 / issue_peak,
         "peak_kind": f"derived: {sms} SMs x 4 schedulers x 1 warp-instr/cycle x {mhz:.0f} MHz",
         "instructions_per_cell": ipc}
     res["clocks"] = clk
@@ -342,13 +365,14 @@ def run_ours(args, rank, world, dist):
 def run_extras(args, B, torch, H, st, cells, dev, stream):
     out = {}
     # ---- e2e through the C ABI with host buffers.  Every step takes its
-    # input state from pinned host memory, advances it one step through
-    # gamer_hydro_step (whose last kernel writes the step result to mapped
-    # host memory) and copies the new state back to pinned host memory.
-    # Two independent states are in flight (double buffering, one handle
-    # each): the copy-in of step k+1 (own stream) overlaps the compute of
-    # step k (the launch stream) and the copy-out of step k-1 (own stream),
-    # as a serving loop over independent states would run.
+    # input state from pinned host memory, advances it through the same
+    # call as the timed step (whose last kernel writes the step result to
+    # mapped host memory) and copies the new state back to pinned host
+    # memory.  Two independent states are in flight (double buffering, one
+    # handle each): the copy-in of step k+1 (own stream) overlaps the
+    # compute of step k (the launch stream) and the copy-out of step k-1
+    # (own stream), as a serving loop over independent states would run.
+    sets = 2 if args.mode == "pair" else 1
     s_in = torch.cuda.Stream(device=dev)
     s_out = torch.cuda.Stream(device=dev)
     solvers = [B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP32, stream=stream) for _ in range(2)]
@@ -369,20 +393,26 @@ def run_extras(args, B, torch, H, st, cells, dev, stream):
         b = it % 2
         S, D = solvers[b], bufs[b]
         if it >= 2:
-            s_in.wait_event(ev_step[b])          # the previous step on this buffer has read u
+            s_in.wait_event(ev_step[b])          # the previous step on this buffer is done with u
+            s_in.wait_event(ev_out[b])           # and its result has been copied out
         with torch.cuda.stream(s_in):
             for l in range(len(D.u)):
                 D.u[l].copy_(host_in[l], non_blocking=True)
             ev_in[b].record(s_in)
         stream.wait_event(ev_in[b])
         if it >= 2:
-            stream.wait_event(ev_out[b])         # u_out of this buffer has been copied out
-        B.gamer_hydro_step(S.h, D, CFL)
+            stream.wait_event(ev_out[b])
+        if sets == 2:
+            B.gamer_hydro_step_pair(S.h, D, CFL)  # result back in u
+            res_bufs = D.u
+        else:
+            B.gamer_hydro_step(S.h, D, CFL)       # result in u_out
+            res_bufs = D.u_out
         ev_step[b].record(stream)
         s_out.wait_event(ev_step[b])
         with torch.cuda.stream(s_out):
             for l in range(len(D.u)):
-                host_out[b][l].copy_(D.u_out[l], non_blocking=True)
+                host_out[b][l].copy_(res_bufs[l], non_blocking=True)
             ev_out[b].record(s_out)
     stream.wait_event(ev_out[0])
     stream.wait_event(ev_out[1])
@@ -392,8 +422,8 @@ def run_extras(args, B, torch, H, st, cells, dev, stream):
         B.gamer_hydro_step_result(S.h)
     ms = e0.elapsed_time(e1) / n_e2e
     nbytes = sum(x.numel() * 4 for x in host_in)
-    out["e2e"] = {"value": cells / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                  "d2h_bytes_per_step": nbytes + 96,
+    out["e2e"] = {"value": cells * sets / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                  "d2h_bytes_per_step": nbytes + 88,      # + the step result (11 x 8 B)
                   "pipeline": "2 independent states in flight; copy-in, step and copy-out on 3 streams"}
     for S in solvers:
         S.close()
@@ -532,9 +562,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": desc, "cells_per_gpu": cells, "precision": "FP32 batched, FP64 reductions",
-                       "step": "gamer_hydro_step: gather + 3 sweeps + CFL dt + conservation/positivity check "
-                               "(one CUDA graph: persistent sweep kernel with fused diagnostics; its last CTA "
-                               "reduces them and writes dt and the result to mapped host memory)",
+                       "step": (STEP_PAIR if args.mode == "pair" else STEP_ONE),
+                       "sweep_sets_per_step": res["sets_per_step"],
                        "l2": "flushed before every timed step (256 MiB write, outside the timed interval)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "roofline": res["roofline"],
