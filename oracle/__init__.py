@@ -36,7 +36,8 @@ VANLEER, MINMOD = 0, 1
 class _Level(C.Structure):
     _fields_ = [("n_groups", C.c_int32), ("pad_", C.c_int32), ("dh", C.c_double),
                 ("u", C.c_void_p), ("u_out", C.c_void_p), ("nbr", C.c_void_p),
-                ("parent", C.c_void_p), ("child", C.c_void_p), ("face_flux", C.c_void_p)]
+                ("parent", C.c_void_p), ("child", C.c_void_p), ("face_flux", C.c_void_p),
+                ("u_new", C.c_void_p), ("coarse_w", C.c_double), ("face_flux2", C.c_void_p)]
 
 
 def build(force: bool = False) -> str:
@@ -73,6 +74,8 @@ def lib():
             L.orc_level_max_speed.argtypes = [C.POINTER(_Level), C.c_double]
             L.orc_cfl_dt.restype = C.c_double
             L.orc_cfl_dt.argtypes = [C.POINTER(_Level), C.c_int, C.c_double, C.c_double]
+            L.orc_cfl_dt_steps.restype = C.c_double
+            L.orc_cfl_dt_steps.argtypes = [C.POINTER(_Level), C.c_int, C.c_double, C.c_double, C.c_int]
             L.orc_gather_block.argtypes = [C.POINTER(_Level), C.c_int, C.c_int, C.c_int, dp]
             L.orc_check.argtypes = [C.POINTER(_Level), C.c_int, C.c_double, dp, C.POINTER(C.c_int64)]
             _lib = L
@@ -164,6 +167,12 @@ class OracleLevels:
         self.child = [None if lv.child is None else np.ascontiguousarray(lv.child, dtype=np.int32)
                       for lv in H.levels]
         self.flux = [np.zeros((lv.n_groups, 3, 3, 5, 16, 16)) if with_flux else None for lv in H.levels]
+        # individual time steps: per level the face fluxes of its two steps
+        # within a coarser step, the weight of its coarse ghosts' time
+        # interpolation, and which of the two flux arrays its sweeps write
+        self.flux2 = None
+        self._cw = [0.0] * self.n
+        self._slot = [0] * self.n
         self._arr = (_Level * max(self.n, 1))()
         self._refresh()
 
@@ -178,6 +187,13 @@ class OracleLevels:
             s.parent = None if self.parent[l] is None else self.parent[l].ctypes.data
             s.child = None if self.child[l] is None else self.child[l].ctypes.data
             s.face_flux = None if self.flux[l] is None else self.flux[l].ctypes.data
+            s.u_new = None
+            s.coarse_w = 0.0
+            s.face_flux2 = None
+            if self.flux2 is not None:
+                s.face_flux = self.flux2[l][self._slot[l]].ctypes.data
+                s.u_new = self.u_out[l].ctypes.data
+                s.coarse_w = self._cw[l]
 
     def advance_level(self, l: int, gamma: float, dt: float, order: int, limiter: int = VANLEER,
                       groups=None) -> None:
@@ -218,9 +234,52 @@ class OracleLevels:
         self.u, self.u_out = self.u_out, self.u
         self._refresh()
 
-    def cfl_dt(self, gamma: float, cfl: float) -> float:
+    def cfl_dt(self, gamma: float, cfl: float, individual: bool = False) -> float:
+        """Eq. CFL; with individual time steps the dt of level 0."""
         self._refresh()
-        return lib().orc_cfl_dt(self._arr, self.n, gamma, cfl)
+        return lib().orc_cfl_dt_steps(self._arr, self.n, gamma, cfl, 1 if individual else 0)
+
+    def cycle_individual(self, gamma: float, dt0: float, limiter: int = VANLEER) -> None:
+        """Individual time steps (Sec. 2.1, readings R18-R20): two steps of
+        level 0 with dt0 (an xyz and a zyx set with one dt, reading R1), so
+        2^(l+1) steps of level l with dt0 / 2^l.  A step of level l is its
+        sweep set from u into u_out (sweep order alternating per level; its
+        coarse ghosts interpolated in time between the coarser level's state
+        before and after that level's sweep set, weight 0 in the first and
+        1/2 in the second of its two steps), then the two steps of the finer
+        level, then the fix-up of level l from the finer level (restriction
+        of the finer state; flux correction with this step's fluxes and the
+        finer fluxes averaged over its two steps), then u <- u_out.  Every
+        level ends in u."""
+        if self.flux2 is None:
+            self.flux2 = [[np.zeros((lv.n_groups, 3, 3, 5, 16, 16)) for _ in range(2)] for lv in self.H.levels]
+        self._level_steps(0, gamma, dt0, limiter)
+
+    def _level_steps(self, l: int, gamma: float, dt: float, limiter: int) -> None:
+        for k in range(2):
+            self._cw[l] = 0.5 * k if l > 0 else 0.0
+            self._slot[l] = k
+            self._refresh()
+            r = lib().orc_level_advance(self._arr, self.n, l, gamma, limiter, dt, k, None, 0)
+            if r != 0:
+                raise ValueError(f"orc_level_advance: {r}")
+            if l + 1 < self.n:
+                self._level_steps(l + 1, gamma, 0.5 * dt, limiter)
+                # fix-up of level l: this step's fluxes against the finer
+                # level's two steps; the finer state is in its u
+                self._slot[l] = k
+                self._refresh()
+                F = self._arr[l + 1]
+                F.u_out = self.u[l + 1].ctypes.data
+                F.face_flux = self.flux2[l + 1][0].ctypes.data
+                F.face_flux2 = self.flux2[l + 1][1].ctypes.data
+                r = lib().orc_level_fixup(self._arr, self.n, l, dt)
+                if r != 0:
+                    raise ValueError(f"orc_level_fixup: {r}")
+            self.u[l], self.u_out[l] = self.u_out[l], self.u[l]
+        self._cw[l] = 0.0
+        self._slot[l] = 0
+        self._refresh()
 
     def max_speed(self, l: int, gamma: float) -> float:
         self._refresh()

@@ -71,6 +71,15 @@ typedef struct {
     const int32_t *parent;
     const int32_t *child;
     double *face_flux;
+    /* individual time steps (Sec. 2.1): */
+    const double *u_new;    /* this level's state after its current sweep set,
+                               read by the finer level's coarse ghosts; NULL: none */
+    double coarse_w;        /* weight of the coarser level's u_new in this level's
+                               coarse ghosts (0 for the first of its two steps,
+                               1/2 for the second) */
+    double *face_flux2;     /* this level's face fluxes of its second step; with
+                               face_flux (first step) averaged by the coarser
+                               level's fix-up; NULL: one step per coarse step */
 } orc_level;
 
 /* ---------------------------------------------------------------- limiters */
@@ -303,6 +312,24 @@ static int level_fetch(const orc_level *L, const double *u, int g, int x,
     return 0;
 }
 
+/* Coarse value for the ghosts of the finer level: the coarser level's state
+ * before its sweep set, or with individual time steps the linear
+ * interpolation in time u + w (u_new - u) to the start of the finer
+ * level's step (w = 0 or 1/2). */
+static int coarse_fetch(const orc_level *C, double w, int g, int x, int y, int z, double val[NV])
+{
+    int r = level_fetch(C, C->u, g, x, y, z, val);
+    if (r != 0 || w == 0.0 || C->u_new == NULL)
+        return r;
+    double b[NV];
+    r = level_fetch(C, C->u_new, g, x, y, z, b);
+    if (r != 0)
+        return r;
+    for (int v = 0; v < NV; v++)
+        val[v] = val[v] + w * (b[v] - val[v]);
+    return 0;
+}
+
 static double minmod2(double a, double b)
 {
     if (a * b > 0.0) {
@@ -315,7 +342,8 @@ static double minmod2(double a, double b)
 /* Conservative linear interpolation with the Min-Mod limiter from the level
  * one coarser (Sec. 2.1 refinement step, Sec. 2.2 ghost zones; reading R8).
  * (x,y,z) is a fine position relative to fine group g, the coarse data is
- * the pre-step state of level lv-1 (reading R7). */
+ * the pre-step state of level lv-1 (reading R7), interpolated in time with
+ * individual time steps (reading R18). */
 static int prolong_fetch(const orc_level *lv, int l, int g, int x, int y, int z,
                          double val[NV])
 {
@@ -334,14 +362,15 @@ static int prolong_fetch(const orc_level *lv, int l, int g, int x, int y, int z,
         sg[a] = (f[a] - 2 * floordiv(f[a], 2)) == 0 ? -1 : 1;
     }
     double U[NV], Um[NV], Up[NV], S[3][NV];
-    if (level_fetch(C, C->u, gc, cc[0], cc[1], cc[2], U) != 0)
+    const double w = lv[l].coarse_w;
+    if (coarse_fetch(C, w, gc, cc[0], cc[1], cc[2], U) != 0)
         return ORC_ERR_MAP;
     for (int a = 0; a < 3; a++) {
         int m[3] = {cc[0], cc[1], cc[2]}, p[3] = {cc[0], cc[1], cc[2]};
         m[a] -= 1;
         p[a] += 1;
-        if (level_fetch(C, C->u, gc, m[0], m[1], m[2], Um) != 0 ||
-            level_fetch(C, C->u, gc, p[0], p[1], p[2], Up) != 0)
+        if (coarse_fetch(C, w, gc, m[0], m[1], m[2], Um) != 0 ||
+            coarse_fetch(C, w, gc, p[0], p[1], p[2], Up) != 0)
             return ORC_ERR_MAP;
         for (int v = 0; v < NV; v++)
             S[a][v] = minmod2(U[v] - Um[v], Up[v] - U[v]);
@@ -526,9 +555,19 @@ int orc_level_fixup(const orc_level *lv, int n_levels, int l, double dt)
                             int T1 = PS * pc[t1] + b1, T2 = PS * pc[t2] + b2;
                             double Gc = C->face_flux[((((size_t)g * 3 + a) * 3 + plane_c) * NV + v) * GS * GS +
                                                      (size_t)T2 * GS + T1];
-                            const double *ff = F->face_flux + ((((size_t)gfq * 3 + a) * 3 + plane_f) * NV + v) * GS * GS;
-                            double Gf = 0.25 * (((ff[(2 * b2) * GS + 2 * b1] + ff[(2 * b2) * GS + 2 * b1 + 1]) +
-                                                 ff[(2 * b2 + 1) * GS + 2 * b1]) + ff[(2 * b2 + 1) * GS + 2 * b1 + 1]);
+                            const size_t fo = ((((size_t)gfq * 3 + a) * 3 + plane_f) * NV + v) * GS * GS;
+                            const size_t k00 = fo + (size_t)(2 * b2) * GS + 2 * b1, k01 = k00 + 1;
+                            const size_t k10 = k00 + GS, k11 = k10 + 1;
+                            double f00 = F->face_flux[k00], f01 = F->face_flux[k01];
+                            double f10 = F->face_flux[k10], f11 = F->face_flux[k11];
+                            if (F->face_flux2 != NULL) {
+                                /* individual time steps: mean over the fine level's two steps */
+                                f00 = 0.5 * (f00 + F->face_flux2[k00]);
+                                f01 = 0.5 * (f01 + F->face_flux2[k01]);
+                                f10 = 0.5 * (f10 + F->face_flux2[k10]);
+                                f11 = 0.5 * (f11 + F->face_flux2[k11]);
+                            }
+                            double Gf = 0.25 * (((f00 + f01) + f10) + f11);
                             int xyz[3];
                             xyz[a] = PS * pc[a] + ca;
                             xyz[t1] = T1;
@@ -572,14 +611,24 @@ double orc_level_max_speed(const orc_level *L, double gamma)
 }
 
 /* Eq. CFL with a safety factor: dt = cfl * min over levels of dh_l / s_l. */
+double orc_cfl_dt_steps(const orc_level *lv, int n_levels, double gamma, double cfl, int individual);
+
 double orc_cfl_dt(const orc_level *lv, int n_levels, double gamma, double cfl)
+{
+    return orc_cfl_dt_steps(lv, n_levels, gamma, cfl, 0);
+}
+
+/* Eq. CFL for the step of level 0: with individual time steps (individual
+ * != 0) level l takes 2^l steps per level-0 step, so its condition
+ * dt / 2^l <= cfl dh_l / s_l bounds the level-0 dt by cfl 2^l dh_l / s_l. */
+double orc_cfl_dt_steps(const orc_level *lv, int n_levels, double gamma, double cfl, int individual)
 {
     double dt = INFINITY;
     for (int l = 0; l < n_levels; l++) {
         if (lv[l].n_groups == 0)
             continue;
         double s = orc_level_max_speed(&lv[l], gamma);
-        double d = lv[l].dh / s;
+        double d = (individual ? ldexp(lv[l].dh, l) : lv[l].dh) / s;
         if (d < dt || d != d)
             dt = d;
     }
