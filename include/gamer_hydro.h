@@ -54,6 +54,7 @@ enum {
 
 enum { GAMER_LIMITER_VANLEER = 0, GAMER_LIMITER_MINMOD = 1 };
 enum { GAMER_FP32 = 0, GAMER_FP64 = 1 };
+enum { GAMER_TIME_STEPS_UNIFORM = 0, GAMER_TIME_STEPS_INDIVIDUAL = 1 };
 
 typedef struct gamer_hydro_s *gamer_hydro_t;
 
@@ -183,6 +184,26 @@ int gamer_hydro_step(gamer_hydro_t h, const gamer_hierarchy_t *H, double cfl);
  * the two sets as two steps.  Captured as a CUDA graph like
  * gamer_hydro_step.  Asynchronous; results via gamer_hydro_step_result. */
 int gamer_hydro_step_pair(gamer_hydro_t h, const gamer_hierarchy_t *H, double cfl);
+
+/* Time stepping of multi-level hierarchies (Sec. 2.1).
+ * GAMER_TIME_STEPS_UNIFORM (default): one dt for every level, as the paper
+ * does with self-gravity.  GAMER_TIME_STEPS_INDIVIDUAL: every level takes
+ * two steps of half its parent's dt, as the paper allows for pure
+ * hydrodynamics; gamer_hydro_step_pair then advances level 0 by two steps
+ * of dt (xyz then zyx) and level l by 2^(l+1) steps of dt / 2^l.  A level's
+ * step is its sweep set, then the two steps of the finer level, whose
+ * coarse ghosts are interpolated linearly in time between the level's
+ * state before and after its sweep set (weight 0, then 1/2), then the
+ * level's fix-up (restriction; flux correction against the finer fluxes
+ * averaged over the finer level's two steps).  Every level's new state is
+ * back in u (no swap).  dt follows Eq. CFL with the factors 2^l:
+ * cfl * min_l 2^l dh_l / s_l (also from gamer_hydro_cfl_dt and
+ * gamer_hydro_diagnose).  gamer_hydro_step refuses multi-level hierarchies
+ * in this mode (GAMER_ERR_UNSUPPORTED); gamer_hydro_advance and
+ * gamer_hydro_advance_all keep one dt for every level.  Changing the mode
+ * waits for the handle's stream and drops its cached graphs and buffers;
+ * the individual mode holds a second face-flux buffer per level. */
+int gamer_hydro_set_time_steps(gamer_hydro_t h, int mode);
 
 /* Result of the last gamer_hydro_step or gamer_hydro_step_pair: the dt it
  * used, the dt the next step will use, the leaf sums of u * dh^3 and the

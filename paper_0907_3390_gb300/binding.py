@@ -18,6 +18,7 @@ from . import build as _build
 
 GAMER_OK, GAMER_ERR_ARG, GAMER_ERR_CUDA, GAMER_ERR_MAP = 0, -1, -2, -3
 GAMER_ERR_TIMEOUT, GAMER_ERR_UNSUPPORTED, GAMER_ERR_STATE = -4, -5, -6
+GAMER_TIME_STEPS_UNIFORM, GAMER_TIME_STEPS_INDIVIDUAL = 0, 1
 GAMER_LIMITER_VANLEER, GAMER_LIMITER_MINMOD = 0, 1
 GAMER_FP32, GAMER_FP64 = 0, 1
 
@@ -26,6 +27,7 @@ EXPORTS = [
     "gamer_hydro_set_parity", "gamer_hydro_get_parity", "gamer_hydro_cfl_dt",
     "gamer_hydro_advance", "gamer_hydro_fixup", "gamer_hydro_advance_all",
     "gamer_hydro_check", "gamer_hydro_diagnose", "gamer_hydro_step", "gamer_hydro_step_pair",
+    "gamer_hydro_set_time_steps",
     "gamer_hydro_step_result",
     "gamer_hydro_diagnose_noalloc", "gamer_hydro_tune", "gamer_hydro_get_config",
     "gamer_hydro_set_profiling", "gamer_hydro_last_error",
@@ -82,6 +84,7 @@ def load(build_if_needed: bool = True) -> C.CDLL:
         L.gamer_hydro_diagnose.argtypes = [H, hp, C.c_double, dp, dp, C.POINTER(C.c_int64)]
         L.gamer_hydro_step.argtypes = [H, hp, C.c_double]
         L.gamer_hydro_step_pair.argtypes = [H, hp, C.c_double]
+        L.gamer_hydro_set_time_steps.argtypes = [H, C.c_int]
         L.gamer_hydro_step_result.argtypes = [H, dp, dp, dp, C.POINTER(C.c_int64)]
         L.gamer_hydro_diagnose_noalloc.argtypes = [C.c_double, C.c_int, hp, C.c_double, vp, dp, dp,
                                                    C.POINTER(C.c_int64)]
@@ -167,6 +170,10 @@ def gamer_hydro_diagnose(h, H, cfl: float):
 
 def gamer_hydro_step(h, H, cfl: float) -> None:
     _check(h, load().gamer_hydro_step(h, H.struct(), cfl))
+
+
+def gamer_hydro_set_time_steps(h, mode: int) -> None:
+    _check(h, load().gamer_hydro_set_time_steps(h, mode))
 
 
 def gamer_hydro_step_pair(h, H, cfl: float) -> None:

@@ -17,7 +17,7 @@ namespace gh {
 template <typename T>
 __global__ void __launch_bounds__(512) k_fixup(const FixArgs<T> a) {
     __shared__ double s_lam;
-    if (threadIdx.x == 0) s_lam = *a.dt / a.dh;   // coarse lambda = dt / dh
+    if (threadIdx.x == 0) s_lam = (*a.dt * a.dts) / a.dh;   // coarse lambda = dt / dh
     __syncthreads();
     const T lam = (T)s_lam;
     const int P = a.list[blockIdx.x];
@@ -72,9 +72,17 @@ __global__ void __launch_bounds__(512) k_fixup(const FixArgs<T> a) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 const T Gc = a.flux_c[((((size_t)g * 3 + ax) * 3 + plane_c) * NV + v) * 256 + T2 * GS + T1];
-                const T* ff = a.flux_f + ((((size_t)gfq * 3 + ax) * 3 + plane_f) * NV + v) * 256;
-                const T Gf = T(0.25) * (((ff[(2 * b2) * GS + 2 * b1] + ff[(2 * b2) * GS + 2 * b1 + 1]) +
-                                         ff[(2 * b2 + 1) * GS + 2 * b1]) + ff[(2 * b2 + 1) * GS + 2 * b1 + 1]);
+                const size_t fo = ((((size_t)gfq * 3 + ax) * 3 + plane_f) * NV + v) * 256;
+                const size_t k00 = fo + (2 * b2) * GS + 2 * b1, k01 = k00 + 1, k10 = k00 + GS, k11 = k10 + 1;
+                T f00 = a.flux_f[k00], f01 = a.flux_f[k01], f10 = a.flux_f[k10], f11 = a.flux_f[k11];
+                if (a.flux_f2 != nullptr) {
+                    // individual time steps: mean over the finer level's two steps
+                    f00 = T(0.5) * (f00 + a.flux_f2[k00]);
+                    f01 = T(0.5) * (f01 + a.flux_f2[k01]);
+                    f10 = T(0.5) * (f10 + a.flux_f2[k10]);
+                    f11 = T(0.5) * (f11 + a.flux_f2[k11]);
+                }
+                const T Gf = T(0.25) * (((f00 + f01) + f10) + f11);
                 if (s > 0) val[v] = val[v] + lam * (Gc - Gf);
                 else val[v] = val[v] - lam * (Gc - Gf);
             }
@@ -287,14 +295,15 @@ __global__ void __launch_bounds__(NT_FIN) k_step_final(const LevelMeta m, const 
 }
 
 cudaError_t launch_step_final(const DiagArgs<float>& a32, const DiagArgs<double>& a64, bool fp64,
-                              const double* dh, double cfl, double* dt, int update_dt, StepOut* out,
-                              StepOut* out_host, cudaStream_t st) {
+                              const double* dh, const double* dscale, double cfl, double* dt, int update_dt,
+                              StepOut* out, StepOut* out_host, cudaStream_t st) {
     LevelMeta m;
     m.n_levels = fp64 ? a64.n_levels : a32.n_levels;
     for (int l = 0; l < m.n_levels; ++l) {
         m.item0[l] = fp64 ? a64.lv[l].item0 : a32.lv[l].item0;
         m.n[l] = fp64 ? a64.lv[l].n_groups : a32.lv[l].n_groups;
         m.dh[l] = dh[l];
+        m.dscale[l] = dscale ? dscale[l] : 1.0;
     }
     const unsigned long long* pm = fp64 ? a64.pg_max : a32.pg_max;
     const double* ps = fp64 ? a64.pg_sum : a32.pg_sum;

@@ -30,12 +30,15 @@ struct LevelArgs {
     T* flux;            // [n][3][3][5][16][16] or nullptr
     const int* parent;  // [n] patch index on level-1, nullptr on level 0
     const T* uc;        // level-1 pre-step state (coarse ghosts)
+    const T* ucn;       // level-1 state after its sweep set (individual time steps), or nullptr
     const int* nbrc;    // level-1 map
     int n_groups;
     int n_groups_c;
     int item0;          // first work item of this level in a multi-level launch
     int pad_;
-    double dh;          // cell width; lambda = dt / dh is formed on the device in FP64
+    double dh;          // cell width; lambda = dt * dts / dh is formed on the device in FP64
+    double dts;         // this level's share of the device dt: 1, or 2^-l with individual time steps
+    double cw;          // time weight of ucn in the coarse ghosts (0 or 1/2)
 };
 
 // Per-group diagnostic sinks (exact max of the signal speed, leaf sums of
@@ -155,9 +158,9 @@ __device__ __forceinline__ T minmod_slope(T l, T c, T r) {
 // (px,py,pz) in coarse group gc.  Coarse data: the coarse level's pre-step
 // state uc, resolved through the coarse region table.  Writes NV values.
 template <typename T>
-__device__ __forceinline__ void prolong(const T* __restrict__ uc, size_t vstride_c,
-                                        const int* s_csrc, const int* s_cmask, int px, int py,
-                                        int pz, int x, int y, int z, T out[NV]) {
+__device__ __forceinline__ void prolong(const T* __restrict__ uc, const T* __restrict__ ucn, T w,
+                                        size_t vstride_c, const int* s_csrc, const int* s_cmask, int px,
+                                        int py, int pz, int x, int y, int z, T out[NV]) {
     const int cx = PS * px + (x >> 1), cy = PS * py + (y >> 1), cz = PS * pz + (z >> 1);
     const T sx = (x & 1) ? T(1) : T(-1);
     const T sy = (y & 1) ? T(1) : T(-1);
@@ -173,10 +176,21 @@ __device__ __forceinline__ void prolong(const T* __restrict__ uc, size_t vstride
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         const T* p = uc + v * vstride_c;
-        T U = p[off[0]];
-        T Sx = minmod_slope(p[off[1]], U, p[off[2]]);
-        T Sy = minmod_slope(p[off[3]], U, p[off[4]]);
-        T Sz = minmod_slope(p[off[5]], U, p[off[6]]);
+        T c[7];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) c[q] = p[off[q]];
+        if (ucn != nullptr) {
+            // individual time steps: the coarse state at the start of this
+            // level's step, linear in time between before and after the
+            // coarse sweep set
+            const T* pn = ucn + v * vstride_c;
+#pragma unroll
+            for (int q = 0; q < 7; ++q) c[q] = c[q] + w * (pn[off[q]] - c[q]);
+        }
+        T U = c[0];
+        T Sx = minmod_slope(c[1], U, c[2]);
+        T Sy = minmod_slope(c[3], U, c[4]);
+        T Sz = minmod_slope(c[5], U, c[6]);
         T t = (sx * Sx + sy * Sy) + sz * Sz;
         out[v] = U + T(0.25) * t;
     }
@@ -205,7 +219,7 @@ __device__ __forceinline__ void gather_block(T* blk, size_t VS, const LevelArgs<
             for (int v = 0; v < NV; ++v) d[v * VS] = p[v * vstride];
         } else {
             T val[NV];
-            prolong<T>(L.uc, vstride_c, s_csrc, s_cmask, ppx, ppy, ppz, xp - NG, yp - NG, zp - NG,
+            prolong<T>(L.uc, L.ucn, (T)L.cw, vstride_c, s_csrc, s_cmask, ppx, ppy, ppz, xp - NG, yp - NG, zp - NG,
                        val);
 #pragma unroll
             for (int v = 0; v < NV; ++v) d[v * VS] = val[v];

@@ -35,6 +35,7 @@ struct LevelCache {
     std::vector<int> fix_list;    // coarse patches visited by the fix-up of this level
     int* d_fix_list = nullptr;
     void* own_flux = nullptr;     // handle-owned face fluxes when the caller gives none
+    void* own_flux2 = nullptr;    // fluxes of a level's second step (individual time steps)
 };
 
 }  // namespace
@@ -77,6 +78,7 @@ struct gamer_hydro_s {
     int f64_threads = 256;
     int f64_chunk = 2048;
     bool tuned = false;
+    int individual = 0;           // individual time steps per level (gamer_hydro_set_time_steps)
 
     // whole steps (gamer_hydro_step): captured CUDA graphs keyed by the
     // launch arguments, replayed on the handle's stream
@@ -154,6 +156,9 @@ void fill_level(LevelArgs<T>& a, const gamer_level_t* L, int l, const gamer_hydr
     a.item0 = 0;
     a.pad_ = 0;
     a.dh = c.dh;
+    a.ucn = nullptr;
+    a.dts = 1.0;
+    a.cw = 0.0;
 }
 
 size_t elem_size(const gamer_hydro_s* h) { return h->precision == GAMER_FP64 ? 8 : 4; }
@@ -186,6 +191,7 @@ void drop_hierarchy(gamer_hydro_t h) {
     for (auto& c : h->lv) {
         cudaFree(c.d_fix_list);
         cudaFree(c.own_flux);
+        cudaFree(c.own_flux2);
     }
     h->lv.clear();
     h->have_version = false;
@@ -287,6 +293,8 @@ int prepare(gamer_hydro_t h, const gamer_hierarchy_t* H) {
         c.dh = H->levels[l].dh;
         if (n > 1 && !H->levels[l].face_flux && c.n_groups > 0)
             CK(h, cudaMalloc(&c.own_flux, (size_t)c.n_groups * FLUX_PG * elem_size(h)));
+        if (n > 1 && h->individual && c.n_groups > 0)
+            CK(h, cudaMalloc(&c.own_flux2, (size_t)c.n_groups * FLUX_PG * elem_size(h)));
         if (l + 1 < n) {
             for (int P = 0; P < 8 * c.n_groups; ++P) {
                 bool take = child[l][P] >= 0;
@@ -413,13 +421,35 @@ int check_level_arg(gamer_hydro_t h, const gamer_hierarchy_t* H, int level) {
 
 // Sweep set of level l reading dt from h->d_dt; `diag` fuses the
 // diagnostics of the new state into the FP32 launch (single level only).
-int advance_level_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, int l, int order) {
+// Per-call options of one level's sweep set (individual time steps): the
+// coarser level's state after its sweep set and the time weight of the
+// coarse ghosts, this level's share of the device dt, the face-flux buffer
+// to write.
+struct LevelStep {
+    const void* ucn = nullptr;
+    double cw = 0.0;
+    double dts = 1.0;
+    void* flux = nullptr;
+};
+
+template <typename T>
+void apply_step(LevelArgs<T>& a, const LevelStep* ls) {
+    if (!ls) return;
+    a.ucn = static_cast<const T*>(ls->ucn);
+    a.cw = ls->cw;
+    a.dts = ls->dts;
+    if (ls->flux) a.flux = static_cast<T*>(ls->flux);
+}
+
+int advance_level_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, int l, int order,
+                       const LevelStep* ls = nullptr) {
     const gamer_level_t* L = H->levels;
     if (L[l].n_groups == 0) return GAMER_OK;
     if (h->precision == GAMER_FP32) {
         SweepArgs<float> a;
         memset(&a, 0, sizeof(a));
         fill_level<float>(a.lv[0], L, l, h);
+        apply_step(a.lv[0], ls);
         a.n_levels = 1;
         a.total = L[l].n_groups;
         a.queue = h->d_queue;
@@ -433,6 +463,7 @@ int advance_level_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, int l, int o
         LevelArgs<double> a;
         memset(&a, 0, sizeof(a));
         fill_level<double>(a, L, l, h);
+        apply_step(a, ls);
         const int chunk = std::min(h->f64_chunk, L[l].n_groups);
         if (h->stage_groups < chunk) {
             cudaFree(h->d_stage);
@@ -449,21 +480,42 @@ int advance_level_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, int l, int o
     return GAMER_OK;
 }
 
-int fixup_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, int l) {
+// Per-call options of a fix-up (individual time steps): the coarse fluxes
+// of this coarse step, the finer fluxes of its two steps, the finer state
+// (after its two steps), the coarse level's share of the device dt.
+struct FixStep {
+    const void* fc = nullptr;
+    const void* ff = nullptr;
+    const void* ff2 = nullptr;
+    const void* uf = nullptr;
+    double dts = 1.0;
+};
+
+int fixup_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, int l, const FixStep* fs = nullptr) {
     const gamer_level_t* L = H->levels;
     const LevelCache& c = h->lv[l];
     if (c.fix_list.empty()) return GAMER_OK;
     const void* fc = L[l].face_flux ? L[l].face_flux : h->lv[l].own_flux;
     const void* ff = L[l + 1].face_flux ? L[l + 1].face_flux : h->lv[l + 1].own_flux;
+    const void* ff2 = nullptr;
+    const void* uf = L[l + 1].u_out;
+    double dts = 1.0;
+    if (fs) {
+        fc = fs->fc;
+        ff = fs->ff;
+        ff2 = fs->ff2;
+        uf = fs->uf;
+        dts = fs->dts;
+    }
     if (h->precision == GAMER_FP32) {
-        FixArgs<float> a{c.d_fix_list, (float*)L[l].u_out, (const float*)L[l + 1].u_out, L[l].nbr,
-                         L[l].child, (const float*)fc, (const float*)ff, L[l].n_groups,
-                         L[l + 1].n_groups, h->d_dt, L[l].dh};
+        FixArgs<float> a{c.d_fix_list, (float*)L[l].u_out, (const float*)uf, L[l].nbr,
+                         L[l].child, (const float*)fc, (const float*)ff, (const float*)ff2, L[l].n_groups,
+                         L[l + 1].n_groups, h->d_dt, L[l].dh, dts};
         CK(h, launch_fixup<float>(a, (int)c.fix_list.size(), h->stream));
     } else {
-        FixArgs<double> a{c.d_fix_list, (double*)L[l].u_out, (const double*)L[l + 1].u_out, L[l].nbr,
-                          L[l].child, (const double*)fc, (const double*)ff, L[l].n_groups,
-                          L[l + 1].n_groups, h->d_dt, L[l].dh};
+        FixArgs<double> a{c.d_fix_list, (double*)L[l].u_out, (const double*)uf, L[l].nbr,
+                          L[l].child, (const double*)fc, (const double*)ff, (const double*)ff2, L[l].n_groups,
+                          L[l + 1].n_groups, h->d_dt, L[l].dh, dts};
         CK(h, launch_fixup<double>(a, (int)c.fix_list.size(), h->stream));
     }
     return GAMER_OK;
@@ -514,7 +566,8 @@ int diagnose_impl(gamer_hydro_t h, const gamer_hierarchy_t* H, double cfl, doubl
             unsigned long long b = h->h_out[l].smax_bits;
             double s;
             memcpy(&s, &b, sizeof(s));
-            double d = H->levels[l].dh / s;
+            // individual time steps: level l takes 2^l steps per dt
+            double d = (h->individual ? std::ldexp(H->levels[l].dh, l) : H->levels[l].dh) / s;
             if (d < dt || d != d) dt = d;
         }
         *dt_out = cfl * dt;
@@ -617,9 +670,86 @@ int enqueue_step(gamer_hydro_t h, const gamer_hierarchy_t* H, cudaStream_t st, b
             e = h->precision == GAMER_FP32 ? launch_diag_groups<float>(d32, h->total_groups, st)
                                            : launch_diag_groups<double>(d64, h->total_groups, st);
         if (e == cudaSuccess && !reduced)
-            e = launch_step_final(d32, d64, h->precision == GAMER_FP64, dh, cfl, h->d_dt, order == 1,
+            e = launch_step_final(d32, d64, h->precision == GAMER_FP64, dh, nullptr, cfl, h->d_dt, order == 1,
                                   h->d_step, h->h_step_dev, st);
         if (e != cudaSuccess) r = cuda_fail(h, e, "step diagnostics");
+    }
+    h->stream = saved;
+    return r;
+}
+
+// Individual time steps (Sec. 2.1; readings R18-R20): two steps of level l
+// with dt0 / 2^l, each its sweep set (u -> u_out; coarse ghosts
+// interpolated in time, weight 0 then 1/2), then the two steps of the finer
+// level, then this level's fix-up from it, then u <-> u_out in lv.  Level
+// l's fluxes go to its own buffer in its first step and to the second
+// buffer in its second step; the fix-up averages the finer level's two.
+int cycle_level(gamer_hydro_t h, gamer_level_t* lv, const gamer_hierarchy_t* Hc, int l) {
+    const int n = Hc->n_levels;
+    auto flux_of = [&](int lev, int k) -> void* {
+        if (k == 1) return h->lv[lev].own_flux2;
+        return lv[lev].face_flux ? lv[lev].face_flux : h->lv[lev].own_flux;
+    };
+    for (int k = 0; k < 2; ++k) {
+        LevelStep ls;
+        ls.dts = std::ldexp(1.0, -l);
+        ls.cw = (l > 0 && k == 1) ? 0.5 : 0.0;
+        ls.ucn = (l > 0 && k == 1) ? lv[l - 1].u_out : nullptr;
+        ls.flux = flux_of(l, k);
+        int r = advance_level_impl(h, Hc, l, k, &ls);
+        if (r) return r;
+        if (l + 1 < n) {
+            if ((r = cycle_level(h, lv, Hc, l + 1))) return r;
+            FixStep fs;
+            fs.fc = flux_of(l, k);
+            fs.ff = flux_of(l + 1, 0);
+            fs.ff2 = flux_of(l + 1, 1);
+            fs.uf = lv[l + 1].u;          // the finer state after its two steps
+            fs.dts = std::ldexp(1.0, -l);
+            if ((r = fixup_impl(h, Hc, l, &fs))) return r;
+        }
+        void* t = lv[l].u_out;
+        lv[l].u_out = const_cast<void*>(lv[l].u);
+        lv[l].u = t;
+    }
+    return GAMER_OK;
+}
+
+// Launch sequence of one individual-time-step cycle of a multi-level
+// hierarchy on stream st (two level-0 steps with one dt), every level back
+// in u, then the diagnostics and the next dt (Eq. CFL with the 2^l factors).
+int enqueue_cycle(gamer_hydro_t h, const gamer_hierarchy_t* H, cudaStream_t st, double cfl) {
+    cudaStream_t saved = h->stream;
+    h->stream = st;
+    gamer_level_t lv[MAXLEV];
+    for (int l = 0; l < H->n_levels; ++l) lv[l] = H->levels[l];
+    gamer_hierarchy_t Hc = *H;
+    Hc.levels = lv;
+    int r = GAMER_OK;
+    cudaError_t e = cudaSuccess;
+    if (h->prof_ev[0]) e = cudaEventRecord(h->prof_ev[0], st);
+    if (e != cudaSuccess) r = cuda_fail(h, e, "cudaEventRecord");
+    if (!r) r = cycle_level(h, lv, &Hc, 0);
+    if (!r && h->prof_ev[1]) {
+        e = cudaEventRecord(h->prof_ev[1], st);
+        if (e != cudaSuccess) r = cuda_fail(h, e, "cudaEventRecord");
+    }
+    if (!r) {
+        DiagArgs<float> d32;
+        DiagArgs<double> d64;
+        diag_args<float>(h, H, d32);      // every level's new state is in u
+        diag_args<double>(h, H, d64);
+        double dh[MAXLEV], ds[MAXLEV];
+        for (int l = 0; l < H->n_levels; ++l) {
+            dh[l] = H->levels[l].dh;
+            ds[l] = std::ldexp(1.0, l);
+        }
+        e = h->precision == GAMER_FP32 ? launch_diag_groups<float>(d32, h->total_groups, st)
+                                       : launch_diag_groups<double>(d64, h->total_groups, st);
+        if (e == cudaSuccess)
+            e = launch_step_final(d32, d64, h->precision == GAMER_FP64, dh, ds, cfl, h->d_dt, 1, h->d_step,
+                                  h->h_step_dev, st);
+        if (e != cudaSuccess) r = cuda_fail(h, e, "cycle diagnostics");
     }
     h->stream = saved;
     return r;
@@ -646,6 +776,7 @@ struct SwappedHierarchy {
 // last CTA also reduces the diagnostics and writes dt and the step result.
 // Otherwise: two whole steps, the second on the swapped hierarchy.
 int enqueue_pair(gamer_hydro_t h, const gamer_hierarchy_t* H, cudaStream_t st, double cfl) {
+    if (h->individual && H->n_levels > 1) return enqueue_cycle(h, H, st, cfl);
     const int n = H->levels[0].n_groups;
     if (!(h->precision == GAMER_FP32 && H->n_levels == 1 && n > 0 && h->pair_n == n)) {
         int r = enqueue_step(h, H, st, true, cfl);
@@ -689,13 +820,16 @@ int diagnose_to_device(gamer_hydro_t h, const gamer_hierarchy_t* H, double cfl) 
     DiagArgs<double> d64;
     diag_args<float>(h, H, d32);
     diag_args<double>(h, H, d64);
-    double dh[MAXLEV];
-    for (int l = 0; l < H->n_levels; ++l) dh[l] = H->levels[l].dh;
+    double dh[MAXLEV], ds[MAXLEV];
+    for (int l = 0; l < H->n_levels; ++l) {
+        dh[l] = H->levels[l].dh;
+        ds[l] = std::ldexp(1.0, l);
+    }
     cudaError_t e = h->precision == GAMER_FP32 ? launch_diag_groups<float>(d32, h->total_groups, h->stream)
                                                : launch_diag_groups<double>(d64, h->total_groups, h->stream);
     if (e == cudaSuccess)
-        e = launch_step_final(d32, d64, h->precision == GAMER_FP64, dh, cfl, h->d_dt, 1, h->d_step, nullptr,
-                              h->stream);
+        e = launch_step_final(d32, d64, h->precision == GAMER_FP64, dh, h->individual ? ds : nullptr, cfl,
+                              h->d_dt, 1, h->d_step, nullptr, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "initial CFL time step");
     return GAMER_OK;
 }
@@ -788,6 +922,21 @@ int gamer_hydro_set_parity(gamer_hydro_t h, int level, int parity) {
     return GAMER_OK;
 }
 
+int gamer_hydro_set_time_steps(gamer_hydro_t h, int mode) {
+    if (!h) return GAMER_ERR_ARG;
+    if (mode != GAMER_TIME_STEPS_UNIFORM && mode != GAMER_TIME_STEPS_INDIVIDUAL)
+        return fail(h, GAMER_ERR_ARG, "unknown time-step mode");
+    if (mode != h->individual) {
+        CK(h, cudaSetDevice(h->device));
+        if (h->stream) CK(h, cudaStreamSynchronize(h->stream));
+        else CK(h, cudaDeviceSynchronize());
+        h->individual = mode;
+        drop_hierarchy(h);            // buffers and graphs depend on the mode
+        h->dt_ready = false;          // and so does Eq. CFL
+    }
+    return GAMER_OK;
+}
+
 int gamer_hydro_get_parity(gamer_hydro_t h, int level, int* parity) {
     if (!h || !parity) return GAMER_ERR_ARG;
     if (level < 0 || level >= 32) return fail(h, GAMER_ERR_ARG, "level must be in [0,32)");
@@ -866,6 +1015,8 @@ int gamer_hydro_advance_all(gamer_hydro_t h, const gamer_hierarchy_t* H, double 
 int gamer_hydro_step(gamer_hydro_t h, const gamer_hierarchy_t* H, double cfl) {
     if (!h) return GAMER_ERR_ARG;
     if (!(cfl > 0.0) || !std::isfinite(cfl)) return fail(h, GAMER_ERR_ARG, "cfl must be positive");
+    if (H && h->individual && H->n_levels > 1)
+        return fail(h, GAMER_ERR_UNSUPPORTED, "individual time steps advance in pairs: use gamer_hydro_step_pair");
     CK(h, cudaSetDevice(h->device));
     int r = prepare(h, H);
     if (r) return r;
@@ -940,7 +1091,7 @@ int gamer_hydro_step_pair(gamer_hydro_t h, const gamer_hierarchy_t* H, double cf
         return GAMER_OK;
     }
     char key[64];
-    snprintf(key, sizeof(key), "pair|%llu|%.17g|", (unsigned long long)h->version, cfl);
+    snprintf(key, sizeof(key), "pair%d|%llu|%.17g|", h->individual, (unsigned long long)h->version, cfl);
     std::string k = key;
     for (int l = 0; l < H->n_levels; ++l) {
         snprintf(key, sizeof(key), "%p,%p,%p;", H->levels[l].u, H->levels[l].u_out, H->levels[l].face_flux);

@@ -34,10 +34,12 @@ struct FixArgs {
     const int* nbr;       // coarse map
     const int* child;     // coarse child map
     const T* flux_c;      // coarse face fluxes
-    const T* flux_f;      // fine face fluxes
+    const T* flux_f;      // fine face fluxes (of the finer level's first step)
+    const T* flux_f2;     // fine face fluxes of its second step (individual time steps), or nullptr
     int n_c, n_f;         // groups on the two levels
     const double* dt;     // device slot holding the time step
     double dh;            // coarse cell width
+    double dts;           // the coarse level's share of the device dt (1 or 2^-l)
 };
 template <typename T>
 cudaError_t launch_fixup(const FixArgs<T>& a, int n_list, cudaStream_t st);
@@ -74,7 +76,7 @@ cudaError_t launch_diag_groups(const DiagArgs<T>& a, int total, cudaStream_t st)
 // One block: per-level reduction of the per-group diagnostics in fixed
 // order, then dt from Eq. CFL (written to *dt when update_dt != 0).
 cudaError_t launch_step_final(const DiagArgs<float>& a32, const DiagArgs<double>& a64, bool fp64,
-                              const double* dh, double cfl, double* dt, int update_dt,
+                              const double* dh, const double* dscale, double cfl, double* dt, int update_dt,
                               StepOut* out, StepOut* out_host, cudaStream_t st);
 cudaError_t launch_set_dt(double* slot, double dt, cudaStream_t st);
 

@@ -5,7 +5,8 @@
 // (strided partials over NT_FIN threads, then a fixed tree), so the result
 // does not depend on which kernel ran it.  dt follows Eq. CFL,
 // dt = cfl * min_l dh_l / s_l in FP64, and the conserved sums are the leaf
-// sums times dh^3, level by level.
+// sums times dh^3, level by level.  With individual time steps level l
+// takes 2^l steps per dt, so its bound on dt is cfl 2^l dh_l / s_l.
 #pragma once
 #include "common.cuh"
 
@@ -28,6 +29,7 @@ struct LevelMeta {
     int item0[MAXLEV];
     int n[MAXLEV];
     double dh[MAXLEV];
+    double dscale[MAXLEV];   // 1, or 2^l with individual time steps (level l takes 2^l steps per dt)
     int n_levels;
 };
 
@@ -83,7 +85,7 @@ __device__ __forceinline__ void step_reduce(const LevelMeta& m, const unsigned l
 #pragma unroll
             for (int v = 0; v < NV; ++v) tot[v] = __dadd_rn(tot[v], __dmul_rn(s_sum[v * NT_FIN], dV));
             const double s = __longlong_as_double((long long)s_max[0]);
-            const double d = m.dh[l] / s;
+            const double d = (m.dh[l] * m.dscale[l]) / s;
             if (d < dtc || d != d) dtc = d;
             nb += s_bad[0];
         }

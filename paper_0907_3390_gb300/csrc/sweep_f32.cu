@@ -275,7 +275,7 @@ __device__ __forceinline__ void build_tab(ItemTab& t, const SweepArgs<float>& a,
         t.level = l;
         t.g = g;
         t.par = L.parent != nullptr ? L.parent[g] : -1;
-        t.lam = (float)(*a.dt / L.dh);
+        t.lam = (float)((*a.dt * L.dts) / L.dh);
     }
 }
 
@@ -298,7 +298,7 @@ __device__ __forceinline__ void prefetch_item(const SweepArgs<float>& a, int ite
 __device__ __noinline__ void prolong_cell(const LevelArgs<float>& L, const ItemTab& t, int x, int y,
                                              int z, float val[NV]) {
     const int lp = t.par & 7;
-    prolong<float>(L.uc, (size_t)L.n_groups_c * 8 * 512, t.csrc, t.cmask, lp & 1, (lp >> 1) & 1,
+    prolong<float>(L.uc, L.ucn, (float)L.cw, (size_t)L.n_groups_c * 8 * 512, t.csrc, t.cmask, lp & 1, (lp >> 1) & 1,
                    (lp >> 2) & 1, x, y, z, val);
 }
 
@@ -618,6 +618,7 @@ __device__ __forceinline__ void finish_launch(const SweepArgs<float>& a, float* 
     m.item0[0] = 0;
     m.n[0] = a.step.n_items;
     m.dh[0] = a.step.dh;
+    m.dscale[0] = 1.0;
     double* s_sum = reinterpret_cast<double*>(sm);
     unsigned long long* s_max = reinterpret_cast<unsigned long long*>(s_sum + NV * NT_FIN);
     long long* s_bad = reinterpret_cast<long long*>(s_max + NT_FIN);

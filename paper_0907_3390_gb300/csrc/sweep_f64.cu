@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(NT64) k_pg_f64(const LevelArgs<double> L, int 
                                                   double* __restrict__ stage) {
     __shared__ int s_tab[160];
     __shared__ double s_lam;
-    if (threadIdx.x == 0) s_lam = *dt / L.dh;   // lambda = dt / dh (Eq. FullstepValue)
+    if (threadIdx.x == 0) s_lam = (*dt * L.dts) / L.dh;   // lambda = dt / dh (Eq. FullstepValue)
     int* s_src = s_tab;
     int* s_mask = s_tab + 32;
     int* s_csrc = s_tab + 64;
