@@ -49,6 +49,9 @@ def parse():
     p.add_argument("--mode", choices=["pair", "step"], default="pair",
                    help="pair: one call = gamer_hydro_step_pair (xyz + zyx sweep sets with one dt, one launch); "
                         "step: one call = gamer_hydro_step (one sweep set)")
+    p.add_argument("--time-steps", choices=["uniform", "individual"], default="uniform",
+                   help="multi-level workloads, --mode pair: one dt for all levels, or every level "
+                        "halving its parent's dt (a call then advances level l by 2^(l+1) steps)")
     p.add_argument("--accuracy", action="store_true",
                    help="instead of timing: per-field L1 / max error of the FP32 path against the FP64 path "
                         "(bit-identical to the FP64 oracle) on every workload, plus positivity and conservation")
@@ -269,6 +272,14 @@ def run_ours(args, rank, world, dist):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     sets = 2 if args.mode == "pair" else 1   # sweep sets (cell-updates per cell) per call
+    individual = args.time_steps == "individual" and len(H.levels) > 1
+    if args.time_steps == "individual" and args.mode != "pair":
+        raise SystemExit("--time-steps individual needs --mode pair")
+    if individual:
+        B.gamer_hydro_set_time_steps(S.h, B.GAMER_TIME_STEPS_INDIVIDUAL)
+    # cell-updates per call: level l takes 2^(l+1) steps per call with individual time steps
+    updates = (sum(lv.n_groups * 4096 * 2 ** (l + 1) for l, lv in enumerate(H.levels)) if individual
+               else cells * sets)
 
     def step():
         if args.mode == "pair":
@@ -318,28 +329,34 @@ def run_ours(args, rank, world, dist):
         t_max = float(t.item())
     else:
         t_max = t_local
-    value = cells * sets * args.steps * world / t_max
-    res = {"value": value, "ms_per_step": 1e3 * t_max / args.steps, "sets_per_step": sets}
+    value = updates * args.steps * world / t_max
+    res = {"value": value, "ms_per_step": 1e3 * t_max / args.steps, "sets_per_step": sets,
+           "updates_per_step": updates, "time_steps": "individual" if individual else "uniform"}
     # kernels per step: one level = the persistent sweep launch alone (it runs
     # the end-of-step reduction in its last CTA); more levels = the sweep
     # launch, one fix-up per coarse level, the diagnostics and the reduction
     n_lev = len(H.levels)
-    res["launches_per_step"] = 1 if n_lev == 1 else sets * (n_lev + 2)
+    if individual:
+        # sweeps 2^(l+1) per level, fix-ups 2^(l+1) per coarse level, diagnostics, reduction
+        res["launches_per_step"] = sum(2 ** (l + 1) for l in range(n_lev)) + \
+            sum(2 ** (l + 1) for l in range(n_lev - 1)) + 2
+    else:
+        res["launches_per_step"] = 1 if n_lev == 1 else sets * (n_lev + 2)
 
     hbm, peak_kind = measured_peaks()
     k_avg = float(np.mean(kern_ms)) / 1e3
-    achieved = BYTES_PER_CELL_F32 * sets * cells / k_avg / 1e9
+    achieved = BYTES_PER_CELL_F32 * updates / k_avg / 1e9
     kname = "sweep_pair" if sets == 2 and n_lev == 1 else "sweep_f32"
     tpc = profile_per_cell("dram_bytes_per_cell", kname)
     res["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                        "frac": achieved / hbm, "peak_kind": f"{peak_kind} copy bandwidth",
-                       "traffic": None if tpc is None else tpc * sets * cells,
+                       "traffic": None if tpc is None or n_lev > 1 else tpc * updates,
                        "kernel": ("k_sweep_pair (xyz and zyx sets of every group: gathers, 2 x 3 sweeps, stores, "
                                   "fused diagnostics and end-of-step reduction, one persistent launch)"
                                   if kname == "sweep_pair" else
                                   "k_sweep_f32 (gather + 3 sweeps + store + fused diagnostics and end-of-step "
                                   "reduction, one persistent launch)"),
-                       "kernel_ms": 1e3 * k_avg, "algorithmic_bytes": BYTES_PER_CELL_F32 * sets * cells}
+                       "kernel_ms": 1e3 * k_avg, "algorithmic_bytes": BYTES_PER_CELL_F32 * updates}
     # the bound that actually limits the kernel: instruction issue (FP32
     # arithmetic of the scheme).  Peak from the unit counts and the clock:
     # SMs x 4 warp schedulers x 1 warp instruction per cycle x max SM clock.
@@ -347,9 +364,9 @@ def run_ours(args, rank, world, dist):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = (clk or {}).get("sm_max_mhz") or 2070.0
     issue_peak = sms * 4 * mhz * 1e6 / 1e12
-    res["roofline_alu"] = None if ipc is None else {
-        "bound": "alu", "achieved": ipc * sets * cells / k_avg / 1e12, "peak": issue_peak, "unit": "T warp-instr/s",
-        "frac": ipc * sets * cells / k_avg / 1e12 / issue_peak,
+    res["roofline_alu"] = None if ipc is None or n_lev > 1 else {
+        "bound": "alu", "achieved": ipc * updates / k_avg / 1e12, "peak": issue_peak, "unit": "T warp-instr/s",
+        "frac": ipc * updates / k_avg / 1e12 / issue_peak,
         "peak_kind": f"derived: {sms} SMs x 4 schedulers x 1 warp-instr/cycle x {mhz:.0f} MHz",
         "instructions_per_cell": ipc}
     res["clocks"] = clk
@@ -357,12 +374,12 @@ def run_ours(args, rank, world, dist):
     res["n_bad"] = n_bad
     extras = {}
     if not args.quick and rank == 0:
-        extras = run_extras(args, B, torch, H, st, cells, dev, stream)
+        extras = run_extras(args, B, torch, H, st, cells, dev, stream, updates)
     S.close()
     return res, extras, cells, desc
 
 
-def run_extras(args, B, torch, H, st, cells, dev, stream):
+def run_extras(args, B, torch, H, st, cells, dev, stream, updates):
     out = {}
     # ---- e2e through the C ABI with host buffers.  Every step takes its
     # input state from pinned host memory, advances it through the same
@@ -376,6 +393,9 @@ def run_extras(args, B, torch, H, st, cells, dev, stream):
     s_in = torch.cuda.Stream(device=dev)
     s_out = torch.cuda.Stream(device=dev)
     solvers = [B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP32, stream=stream) for _ in range(2)]
+    if args.time_steps == "individual" and len(H.levels) > 1:
+        for S in solvers:
+            B.gamer_hydro_set_time_steps(S.h, B.GAMER_TIME_STEPS_INDIVIDUAL)
     bufs = [B.DeviceHierarchy(H, st, torch.float32, device=dev) for _ in range(2)]
     host_in = [x.cpu().pin_memory() for x in bufs[0].u]
     host_out = [[torch.empty_like(x).pin_memory() for x in host_in] for _ in range(2)]
@@ -422,7 +442,7 @@ def run_extras(args, B, torch, H, st, cells, dev, stream):
         B.gamer_hydro_step_result(S.h)
     ms = e0.elapsed_time(e1) / n_e2e
     nbytes = sum(x.numel() * 4 for x in host_in)
-    out["e2e"] = {"value": cells * sets / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+    out["e2e"] = {"value": updates / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                   "d2h_bytes_per_step": nbytes + 88,      # + the step result (11 x 8 B)
                   "pipeline": "2 independent states in flight; copy-in, step and copy-out on 3 streams"}
     for S in solvers:
@@ -564,6 +584,8 @@ def main():
             "config": {"workload": desc, "cells_per_gpu": cells, "precision": "FP32 batched, FP64 reductions",
                        "step": (STEP_PAIR if args.mode == "pair" else STEP_ONE),
                        "sweep_sets_per_step": res["sets_per_step"],
+                       "time_steps": res["time_steps"],
+                       "cell_updates_per_step": res["updates_per_step"],
                        "l2": "flushed before every timed step (256 MiB write, outside the timed interval)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "roofline": res["roofline"],
