@@ -77,6 +77,8 @@ def _wl_amr(kind):
         from paper_0907_3390_gb300 import workloads as W
         if kind == "amr3":
             return W.amr_grf()
+        if kind == "amr4sedov":
+            return W.amr_stress("sedov")
         return W.amr_stress("lognormal")
     return make
 
@@ -90,6 +92,8 @@ WORKLOADS = {
     "amr3": ("3 levels over a 128^3 base, 4096/9000/21000 patches, lognormal k^-2 density", _wl_amr("amr3")),
     "amr4": ("4 levels, 32768 patches, lognormal sigma 2.5 density, converging flows up to Mach 20",
              _wl_amr("amr4")),
+    "amr4sedov": ("4 levels, 32768 patches, Sedov point blast (E = 1 in one finest cell, rho 1, P 1e-5)",
+                  _wl_amr("amr4sedov")),
 }
 
 
