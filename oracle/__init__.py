@@ -74,6 +74,10 @@ def lib():
             L.orc_level_max_speed.argtypes = [C.POINTER(_Level), C.c_double]
             L.orc_cfl_dt.restype = C.c_double
             L.orc_cfl_dt.argtypes = [C.POINTER(_Level), C.c_int, C.c_double, C.c_double]
+            L.orc_flag_level.argtypes = [C.POINTER(_Level), C.c_int, C.c_int, C.c_double, C.c_int, C.c_double,
+                                         C.c_int, C.POINTER(C.c_uint32)]
+            L.orc_refine_fill.argtypes = [C.POINTER(_Level), C.c_int, C.c_int, C.POINTER(C.c_int32),
+                                          C.POINTER(C.c_int32), dp, C.c_int, dp]
             L.orc_cfl_dt_steps.restype = C.c_double
             L.orc_cfl_dt_steps.argtypes = [C.POINTER(_Level), C.c_int, C.c_double, C.c_double, C.c_int]
             L.orc_gather_block.argtypes = [C.POINTER(_Level), C.c_int, C.c_int, C.c_int, dp]
@@ -284,6 +288,31 @@ class OracleLevels:
     def max_speed(self, l: int, gamma: float) -> float:
         self._refresh()
         return lib().orc_level_max_speed(C.byref(self._arr[l]), gamma)
+
+    def flag_level(self, l: int, gamma: float, criterion: int, threshold: float, n_buffer: int) -> np.ndarray:
+        """Per-patch flag-buffer masks of level l (orc_flag_level)."""
+        self._refresh()
+        masks = np.zeros(8 * self.H.levels[l].n_groups, dtype=np.uint32)
+        r = lib().orc_flag_level(self._arr, self.n, l, gamma, criterion, threshold, n_buffer,
+                                 masks.ctypes.data_as(C.POINTER(C.c_uint32)))
+        if r != 0:
+            raise ValueError(f"orc_flag_level: {r}")
+        return masks
+
+    def refine_fill(self, l: int, parent_new, inherit, u_old) -> np.ndarray:
+        """Data of a rebuilt level l+1 (orc_refine_fill) from this level's u."""
+        self._refresh()
+        pn = np.ascontiguousarray(parent_new, dtype=np.int32)
+        ih = np.ascontiguousarray(inherit, dtype=np.int32)
+        n_new = len(pn)
+        uo = np.ascontiguousarray(u_old if u_old is not None else np.zeros((5, 8, 512)), dtype=np.float64)
+        n_old = uo.shape[1] // 8
+        out = np.empty((5, 8 * n_new, 8, 8, 8))
+        r = lib().orc_refine_fill(self._arr, l, n_new, pn.ctypes.data_as(C.POINTER(C.c_int32)),
+                                  ih.ctypes.data_as(C.POINTER(C.c_int32)), _dp(uo), n_old, _dp(out))
+        if r != 0:
+            raise ValueError(f"orc_refine_fill: {r}")
+        return out
 
     def check(self, gamma: float):
         self._refresh()

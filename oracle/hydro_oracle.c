@@ -54,6 +54,7 @@
 #define PD 22     /* padded patch-group size GS + 2*NG                */
 
 enum { ORC_VANLEER = 0, ORC_MINMOD = 1 };
+#define MAXLV 16
 enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_MAP = -3 };
 
 /* One refinement level as the oracle sees it.  All arrays are host memory.
@@ -580,6 +581,138 @@ int orc_level_fixup(const orc_level *lv, int n_levels, int l, double dt)
                         }
             }
         }
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------ regridding */
+
+/* Quantity of the refinement criterion at a group-local position (density
+ * or pressure, Eqs. ShockTube_RefineCriterion and BlastWave_RefineCriterion):
+ * 0 on success, 1 if the position only exists on the coarser level. */
+static int crit_value(const orc_level *L, int g, int x, int y, int z, int criterion, double gamma, double *q)
+{
+    double u[NV];
+    int r = level_fetch(L, L->u, g, x, y, z, u);
+    if (r != 0)
+        return r;
+    *q = criterion == 1 ? orc_pressure(u, gamma) : u[0];
+    return 0;
+}
+
+/* Flag step of the refinement-map rebuild (Sec. 2.1 step 4; readings R21,
+ * R22).  A cell of level l satisfies
+ *   criterion 0: max over axes of |rho(+1) - rho(-1)| / (2 |rho|) >= threshold
+ *                (the relative change of density across one cell width),
+ *   criterion 1: the same for the pressure,
+ *   criterion 2: rho > threshold,
+ * where a neighbour that only exists on the coarser level is replaced by the
+ * cell itself.  Around every such cell the flag buffer is the cube of
+ * 1 + 2 n_buffer cells; masks[p] of patch p gets bit (dz+1)*9+(dy+1)*3+(dx+1)
+ * for every patch at offset (dx,dy,dz) (bit 13: p itself) that the buffer of
+ * one of its cells reaches.  0 <= n_buffer <= 8. */
+int orc_flag_level(const orc_level *lv, int n_levels, int l, double gamma, int criterion,
+                   double threshold, int n_buffer, uint32_t *masks)
+{
+    if (l < 0 || l >= n_levels || n_buffer < 0 || n_buffer > PS || criterion < 0 || criterion > 2)
+        return ORC_ERR_ARG;
+    const orc_level *L = &lv[l];
+    for (int p = 0; p < 8 * L->n_groups; p++)
+        masks[p] = 0u;
+    for (int g = 0; g < L->n_groups; g++)
+        for (int z = 0; z < GS; z++)
+            for (int y = 0; y < GS; y++)
+                for (int x = 0; x < GS; x++) {
+                    double q0;
+                    if (crit_value(L, g, x, y, z, criterion == 2 ? 0 : criterion, gamma, &q0) != 0)
+                        return ORC_ERR_MAP;
+                    int hit;
+                    if (criterion == 2) {
+                        hit = q0 > threshold;
+                    } else {
+                        double rmax = 0.0;
+                        int c[3] = {x, y, z};
+                        for (int a = 0; a < 3; a++) {
+                            double qm, qp;
+                            int m[3] = {c[0], c[1], c[2]}, pp[3] = {c[0], c[1], c[2]};
+                            m[a] -= 1;
+                            pp[a] += 1;
+                            int rm = crit_value(L, g, m[0], m[1], m[2], criterion, gamma, &qm);
+                            int rp = crit_value(L, g, pp[0], pp[1], pp[2], criterion, gamma, &qp);
+                            if (rm < 0 || rp < 0)
+                                return ORC_ERR_MAP;
+                            if (rm == 1)
+                                qm = q0;
+                            if (rp == 1)
+                                qp = q0;
+                            double r = fabs(qp - qm) / (2.0 * fabs(q0));
+                            if (r > rmax)
+                                rmax = r;
+                        }
+                        hit = rmax >= threshold;
+                    }
+                    if (!hit)
+                        continue;
+                    int lp = ((z / PS) * 2 + (y / PS)) * 2 + (x / PS);
+                    int pc[3] = {x % PS, y % PS, z % PS};
+                    int lo[3], hi[3];
+                    for (int a = 0; a < 3; a++) {
+                        lo[a] = pc[a] - n_buffer < 0 ? -1 : 0;
+                        hi[a] = pc[a] + n_buffer > PS - 1 ? 1 : 0;
+                    }
+                    uint32_t m = 0u;
+                    for (int dz = lo[2]; dz <= hi[2]; dz++)
+                        for (int dy = lo[1]; dy <= hi[1]; dy++)
+                            for (int dx = lo[0]; dx <= hi[0]; dx++)
+                                m |= 1u << ((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1));
+                    masks[8 * g + lp] |= m;
+                }
+    return ORC_OK;
+}
+
+/* Refinement step (Sec. 2.1 step 4): the data of a rebuilt level.  lv[0..l]
+ * are the levels up to the new level's parent level l; the new level has
+ * n_new groups whose parents (patches of level l) are parent_new.  Group i
+ * copies old group inherit[i] of the previous fine level (u_old, n_old
+ * groups) when inherit[i] >= 0, and otherwise fills every cell by Min-Mod
+ * interpolation from level l (R8), into u_new. */
+int orc_refine_fill(const orc_level *lv, int l, int n_new, const int32_t *parent_new,
+                    const int32_t *inherit, const double *u_old, int n_old, double *u_new)
+{
+    orc_level tmp[MAXLV + 1];
+    if (l < 0 || l >= MAXLV)
+        return ORC_ERR_ARG;
+    for (int k = 0; k <= l; k++) {
+        tmp[k] = lv[k];
+        tmp[k].u_new = NULL;
+        tmp[k].coarse_w = 0.0;
+    }
+    orc_level *F = &tmp[l + 1];
+    memset(F, 0, sizeof(*F));
+    F->n_groups = n_new;
+    F->dh = 0.5 * lv[l].dh;
+    F->parent = parent_new;
+    F->u_out = u_new;
+    const size_t cells = (size_t)PS * PS * PS;
+    for (int i = 0; i < n_new; i++) {
+        if (inherit[i] >= 0) {
+            if (inherit[i] >= n_old)
+                return ORC_ERR_ARG;
+            for (int v = 0; v < NV; v++)
+                memcpy(u_new + ((size_t)v * 8 * n_new + 8 * (size_t)i) * cells,
+                       u_old + ((size_t)v * 8 * n_old + 8 * (size_t)inherit[i]) * cells,
+                       sizeof(double) * 8 * cells);
+            continue;
+        }
+        for (int z = 0; z < GS; z++)
+            for (int y = 0; y < GS; y++)
+                for (int x = 0; x < GS; x++) {
+                    double val[NV];
+                    if (prolong_fetch(tmp, l + 1, i, x, y, z, val) != 0)
+                        return ORC_ERR_MAP;
+                    for (int v = 0; v < NV; v++)
+                        u_new[cell_index(F, i, v, x, y, z)] = val[v];
+                }
     }
     return ORC_OK;
 }

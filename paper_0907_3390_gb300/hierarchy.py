@@ -177,26 +177,47 @@ def build_hierarchy(base_npg: tuple[int, int, int], score_fn, n_levels: int,
             refine = [int(p) for p in eligible if score[p] > 0]
         if not refine:
             break
-        child = np.full(8 * cur.n_groups, -1, dtype=np.int32)
-        fine_coords = np.empty((len(refine), 3), dtype=np.int64)
-        for i, p in enumerate(refine):
-            child[p] = i
-            g, lp = divmod(p, 8)
-            fine_coords[i] = _patch_key(cur.coords[g], lp)
-        cur.child = child
-        n_f = len(refine)
-        nbr = np.empty((n_f, 26), dtype=np.int32)
-        for i, p in enumerate(refine):
-            k = fine_coords[i]
-            for (dx, dy, dz) in DIRS:
-                q = ((k[0] + dx) % ext_p[0], (k[1] + dy) % ext_p[1], (k[2] + dz) % ext_p[2])
-                qp = lookup[q]
-                nbr[i, dir_index(dx, dy, dz)] = child[qp] if child[qp] >= 0 else -1
-        fine = LevelMap(n_groups=n_f, dh=cur.dh / 2, nbr=nbr,
-                        parent=np.asarray(refine, dtype=np.int32),
-                        coords=fine_coords, extent=ext_p)
-        levels.append(fine)
+        levels.append(refine_level(cur, refine))
     return H
+
+
+def refine_level(cur: LevelMap, refine) -> LevelMap:
+    """The next finer level made of the children of the listed patches of
+    ``cur`` (one patch group per refined patch, numbered in list order);
+    sets ``cur.child``.  Every refined patch must have its 26 same-level
+    neighbours (periodic wrap)."""
+    ext_p = tuple(2 * e for e in cur.extent)
+    lookup = {}
+    for g in range(cur.n_groups):
+        for lp in range(8):
+            lookup[_patch_key(cur.coords[g], lp)] = 8 * g + lp
+    refine = [int(p) for p in refine]
+    child = np.full(8 * cur.n_groups, -1, dtype=np.int32)
+    fine_coords = np.empty((len(refine), 3), dtype=np.int64)
+    for i, p in enumerate(refine):
+        child[p] = i
+        g, lp = divmod(p, 8)
+        fine_coords[i] = _patch_key(cur.coords[g], lp)
+    cur.child = child
+    n_f = len(refine)
+    nbr = np.empty((n_f, 26), dtype=np.int32)
+    for i, p in enumerate(refine):
+        k = fine_coords[i]
+        for (dx, dy, dz) in DIRS:
+            q = ((k[0] + dx) % ext_p[0], (k[1] + dy) % ext_p[1], (k[2] + dz) % ext_p[2])
+            qp = lookup[q]
+            nbr[i, dir_index(dx, dy, dz)] = child[qp] if child[qp] >= 0 else -1
+    return LevelMap(n_groups=n_f, dh=cur.dh / 2, nbr=nbr, parent=np.asarray(refine, dtype=np.int32),
+                    coords=fine_coords, extent=ext_p)
+
+
+def patch_lookup(level: LevelMap) -> dict:
+    """{(px, py, pz) patch coordinates on the level: patch index}."""
+    out = {}
+    for g in range(level.n_groups):
+        for lp in range(8):
+            out[_patch_key(level.coords[g], lp)] = 8 * g + lp
+    return out
 
 
 def leaf_mask(level: LevelMap) -> np.ndarray:
