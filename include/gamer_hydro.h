@@ -55,6 +55,7 @@ enum {
 enum { GAMER_LIMITER_VANLEER = 0, GAMER_LIMITER_MINMOD = 1 };
 enum { GAMER_FP32 = 0, GAMER_FP64 = 1 };
 enum { GAMER_TIME_STEPS_UNIFORM = 0, GAMER_TIME_STEPS_INDIVIDUAL = 1 };
+enum { GAMER_FLAG_DENSITY_GRADIENT = 0, GAMER_FLAG_PRESSURE_GRADIENT = 1, GAMER_FLAG_DENSITY = 2 };
 
 typedef struct gamer_hydro_s *gamer_hydro_t;
 
@@ -204,6 +205,38 @@ int gamer_hydro_step_pair(gamer_hydro_t h, const gamer_hierarchy_t *H, double cf
  * waits for the handle's stream and drops its cached graphs and buffers;
  * the individual mode holds a second face-flux buffer per level. */
 int gamer_hydro_set_time_steps(gamer_hydro_t h, int mode);
+
+/* Flag step of the refinement-map rebuild (Sec. 2.1 step 4) on level
+ * `level` of H (its u).  A cell is flagged when
+ *   GAMER_FLAG_DENSITY_GRADIENT / GAMER_FLAG_PRESSURE_GRADIENT: the largest
+ *     relative change of density / pressure across one cell width,
+ *     max over x, y, z of |q(+1) - q(-1)| / (2 |q|), reaches threshold
+ *     (Eqs. ShockTube_RefineCriterion, BlastWave_RefineCriterion; a
+ *     neighbour that only exists on the coarser level counts as the cell
+ *     itself, outflow edges as zero gradient);
+ *   GAMER_FLAG_DENSITY: rho > threshold;
+ * evaluated in FP64 whatever the handle's precision.  Every flagged cell
+ * has a flag buffer, the cube of 1 + 2 n_buffer cells around it
+ * (0 <= n_buffer <= 8); masks (device, [8 n_groups] uint32) receives per
+ * patch the bit (dz+1)*9 + (dy+1)*3 + (dx+1) of every patch offset that
+ * the buffers of its cells reach (bit 13: the patch itself).  The caller
+ * combines the masks into flags and rebuilds the maps (the library's
+ * Python side does, in paper_0907_3390_gb300/regrid.py).  Asynchronous. */
+int gamer_hydro_flag(gamer_hydro_t h, const gamer_hierarchy_t *H, int level, int criterion, double threshold,
+                     int n_buffer, uint32_t *masks);
+
+/* Refinement step: the data of a rebuilt level l+1 whose n_new patch groups
+ * have the parent patches parent_new (device, patch indices on level l =
+ * `level` of H).  Group i copies group inherit[i] (device, or -1) of the
+ * previous state u_old of that level (n_old groups, device, may be NULL if
+ * nothing inherits); the others are filled cell by cell by Min-Mod
+ * interpolation (R8) from level l's u.  u_new: device [5][8 n_new][8][8][8],
+ * 16-byte aligned.  The parents must be properly nested (their 26
+ * neighbours on level l exist), else GAMER_ERR_MAP; this is checked on the
+ * host, so the call synchronises the device. */
+int gamer_hydro_refine_fill(gamer_hydro_t h, const gamer_hierarchy_t *H, int level, int n_new,
+                            const int32_t *parent_new, const int32_t *inherit, const void *u_old, int n_old,
+                            void *u_new);
 
 /* Result of the last gamer_hydro_step or gamer_hydro_step_pair: the dt it
  * used, the dt the next step will use, the leaf sums of u * dh^3 and the

@@ -19,6 +19,7 @@ from . import build as _build
 GAMER_OK, GAMER_ERR_ARG, GAMER_ERR_CUDA, GAMER_ERR_MAP = 0, -1, -2, -3
 GAMER_ERR_TIMEOUT, GAMER_ERR_UNSUPPORTED, GAMER_ERR_STATE = -4, -5, -6
 GAMER_TIME_STEPS_UNIFORM, GAMER_TIME_STEPS_INDIVIDUAL = 0, 1
+GAMER_FLAG_DENSITY_GRADIENT, GAMER_FLAG_PRESSURE_GRADIENT, GAMER_FLAG_DENSITY = 0, 1, 2
 GAMER_LIMITER_VANLEER, GAMER_LIMITER_MINMOD = 0, 1
 GAMER_FP32, GAMER_FP64 = 0, 1
 
@@ -27,7 +28,7 @@ EXPORTS = [
     "gamer_hydro_set_parity", "gamer_hydro_get_parity", "gamer_hydro_cfl_dt",
     "gamer_hydro_advance", "gamer_hydro_fixup", "gamer_hydro_advance_all",
     "gamer_hydro_check", "gamer_hydro_diagnose", "gamer_hydro_step", "gamer_hydro_step_pair",
-    "gamer_hydro_set_time_steps",
+    "gamer_hydro_set_time_steps", "gamer_hydro_flag", "gamer_hydro_refine_fill",
     "gamer_hydro_step_result",
     "gamer_hydro_diagnose_noalloc", "gamer_hydro_tune", "gamer_hydro_get_config",
     "gamer_hydro_set_profiling", "gamer_hydro_last_error",
@@ -85,6 +86,8 @@ def load(build_if_needed: bool = True) -> C.CDLL:
         L.gamer_hydro_step.argtypes = [H, hp, C.c_double]
         L.gamer_hydro_step_pair.argtypes = [H, hp, C.c_double]
         L.gamer_hydro_set_time_steps.argtypes = [H, C.c_int]
+        L.gamer_hydro_flag.argtypes = [H, hp, C.c_int, C.c_int, C.c_double, C.c_int, vp]
+        L.gamer_hydro_refine_fill.argtypes = [H, hp, C.c_int, C.c_int, vp, vp, vp, C.c_int, vp]
         L.gamer_hydro_step_result.argtypes = [H, dp, dp, dp, C.POINTER(C.c_int64)]
         L.gamer_hydro_diagnose_noalloc.argtypes = [C.c_double, C.c_int, hp, C.c_double, vp, dp, dp,
                                                    C.POINTER(C.c_int64)]
@@ -176,6 +179,20 @@ def gamer_hydro_set_time_steps(h, mode: int) -> None:
     _check(h, load().gamer_hydro_set_time_steps(h, mode))
 
 
+def gamer_hydro_flag(h, H, level: int, criterion: int, threshold: float, n_buffer: int, masks) -> None:
+    """masks: device uint32 tensor [8 n_groups] of the level (written)."""
+    _check(h, load().gamer_hydro_flag(h, H.struct(), level, criterion, threshold, n_buffer, masks.data_ptr()))
+
+
+def gamer_hydro_refine_fill(h, H, level: int, parent_new, inherit, u_old, u_new) -> None:
+    """parent_new, inherit: device int32 tensors [n_new]; u_old: device state
+    of the previous level l+1 or None; u_new: device state [5, 8 n_new, 8, 8, 8]."""
+    n_new = int(parent_new.numel())
+    n_old = 0 if u_old is None else int(u_old.shape[1]) // 8
+    _check(h, load().gamer_hydro_refine_fill(h, H.struct(), level, n_new, parent_new.data_ptr(), inherit.data_ptr(),
+                                              None if u_old is None else u_old.data_ptr(), n_old, u_new.data_ptr()))
+
+
 def gamer_hydro_step_pair(h, H, cfl: float) -> None:
     """xyz + zyx sweep sets with one dt; the result is back in H.u (no swap)."""
     _check(h, load().gamer_hydro_step_pair(h, H.struct(), cfl))
@@ -239,7 +256,9 @@ class DeviceHierarchy:
         self.dtype = dtype
         self.device = torch.device(device)
         n = H.n_levels
-        self.u = [torch.as_tensor(np.ascontiguousarray(s), dtype=dtype).to(self.device) for s in states]
+        # states: host arrays, or device tensors of this dtype that are used as they are
+        self.u = [s if (torch.is_tensor(s) and s.is_cuda and s.dtype == dtype and s.is_contiguous())
+                  else torch.as_tensor(np.ascontiguousarray(s), dtype=dtype).to(self.device) for s in states]
         self.u_out = [torch.empty_like(x) for x in self.u]
         self.nbr = [torch.as_tensor(np.ascontiguousarray(lv.nbr, dtype=np.int32)).to(self.device)
                     for lv in H.levels]

@@ -8,7 +8,9 @@ Each translation unit is compiled in parallel, then linked with
 * sweep_f64.cu, aux_kernels.cu: ``-fmad=false`` so FP64 results round
   exactly as the plain definition of the scheme;
 * hydro_api.cu: host code of the C ABI;
-* noalloc.cu: the allocation-free diagnostics entry point.
+* noalloc.cu: the allocation-free diagnostics entry point;
+* regrid.cu: flag step and refinement fill of the refinement-map rebuild,
+  ``-fmad=false`` (FP64 criteria in their plain order).
 """
 from __future__ import annotations
 
@@ -33,6 +35,7 @@ UNITS = {
     "aux_kernels.cu": ["-fmad=false"],
     "hydro_api.cu": [],
     "noalloc.cu": [],
+    "regrid.cu": ["-fmad=false"],
 }
 
 

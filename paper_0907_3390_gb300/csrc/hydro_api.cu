@@ -2,6 +2,7 @@
 // hierarchy snapshots, scratch management, launch sequencing, CUDA-graph
 // replay of whole steps, and error reporting.
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -933,6 +934,82 @@ int gamer_hydro_set_time_steps(gamer_hydro_t h, int mode) {
         h->individual = mode;
         drop_hierarchy(h);            // buffers and graphs depend on the mode
         h->dt_ready = false;          // and so does Eq. CFL
+    }
+    return GAMER_OK;
+}
+
+int gamer_hydro_flag(gamer_hydro_t h, const gamer_hierarchy_t* H, int level, int criterion, double threshold,
+                     int n_buffer, uint32_t* masks) {
+    if (!h) return GAMER_ERR_ARG;
+    if (criterion < GAMER_FLAG_DENSITY_GRADIENT || criterion > GAMER_FLAG_DENSITY)
+        return fail(h, GAMER_ERR_ARG, "unknown refinement criterion");
+    if (n_buffer < 0 || n_buffer > PS) return fail(h, GAMER_ERR_ARG, "n_buffer must be in [0, 8]");
+    if (!masks) return fail(h, GAMER_ERR_ARG, "masks is NULL");
+    CK(h, cudaSetDevice(h->device));
+    int r = prepare(h, H);
+    if (r) return r;
+    if ((r = check_level_arg(h, H, level))) return r;
+    const gamer_level_t& L = H->levels[level];
+    if (L.n_groups == 0) return GAMER_OK;
+    if (!L.u) return fail(h, GAMER_ERR_ARG, "u is NULL");
+    if (h->precision == GAMER_FP32) {
+        FlagArgs<float> a{static_cast<const float*>(L.u), L.nbr, L.n_groups, criterion, threshold, n_buffer,
+                          h->gamma, masks};
+        CK(h, launch_flag<float>(a, h->stream));
+    } else {
+        FlagArgs<double> a{static_cast<const double*>(L.u), L.nbr, L.n_groups, criterion, threshold, n_buffer,
+                           h->gamma, masks};
+        CK(h, launch_flag<double>(a, h->stream));
+    }
+    return GAMER_OK;
+}
+
+int gamer_hydro_refine_fill(gamer_hydro_t h, const gamer_hierarchy_t* H, int level, int n_new,
+                            const int32_t* parent_new, const int32_t* inherit, const void* u_old, int n_old,
+                            void* u_new) {
+    if (!h) return GAMER_ERR_ARG;
+    if (n_new < 0 || n_old < 0) return fail(h, GAMER_ERR_ARG, "negative group count");
+    if (n_new == 0) return GAMER_OK;
+    if (!parent_new || !inherit || !u_new) return fail(h, GAMER_ERR_ARG, "parent_new, inherit and u_new are required");
+    if (reinterpret_cast<uintptr_t>(u_new) % 16 || reinterpret_cast<uintptr_t>(u_old) % 16)
+        return fail(h, GAMER_ERR_ARG, "u_new and u_old must be 16-byte aligned");
+    CK(h, cudaSetDevice(h->device));
+    int r = prepare(h, H);
+    if (r) return r;
+    if ((r = check_level_arg(h, H, level))) return r;
+    const gamer_level_t& L = H->levels[level];
+    if (!L.u) return fail(h, GAMER_ERR_ARG, "u is NULL");
+    // validate on the host: parents in range and properly nested (the 26
+    // neighbours of every parent patch exist on its level), inheritance in range
+    std::vector<int> par(n_new), inh(n_new), nbr((size_t)L.n_groups * 26);
+    CK(h, cudaMemcpy(par.data(), parent_new, sizeof(int) * n_new, cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(inh.data(), inherit, sizeof(int) * n_new, cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(nbr.data(), L.nbr, sizeof(int) * nbr.size(), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n_new; ++i) {
+        if (inh[i] >= n_old || inh[i] < -1) return fail(h, GAMER_ERR_ARG, "inherit entry out of range");
+        if (inh[i] >= 0) {
+            if (!u_old) return fail(h, GAMER_ERR_ARG, "u_old is NULL but groups inherit");
+            continue;
+        }
+        const int P = par[i];
+        if (P < 0 || P >= 8 * L.n_groups) return fail(h, GAMER_ERR_MAP, "parent_new entry out of range");
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int lp = P & 7;
+                    int q[3] = {(lp & 1) + dx, ((lp >> 1) & 1) + dy, ((lp >> 2) & 1) + dz};
+                    if (resolve_patch(nbr, P >> 3, q) < 0)
+                        return fail(h, GAMER_ERR_MAP, "a parent patch of the new level is not properly nested");
+                }
+    }
+    if (h->precision == GAMER_FP32) {
+        RefineArgs<float> a{static_cast<const float*>(L.u), L.nbr, L.n_groups, parent_new, inherit,
+                            static_cast<const float*>(u_old), n_old, static_cast<float*>(u_new), n_new};
+        CK(h, launch_refine<float>(a, h->stream));
+    } else {
+        RefineArgs<double> a{static_cast<const double*>(L.u), L.nbr, L.n_groups, parent_new, inherit,
+                             static_cast<const double*>(u_old), n_old, static_cast<double*>(u_new), n_new};
+        CK(h, launch_refine<double>(a, h->stream));
     }
     return GAMER_OK;
 }

@@ -44,6 +44,36 @@ struct FixArgs {
 template <typename T>
 cudaError_t launch_fixup(const FixArgs<T>& a, int n_list, cudaStream_t st);
 
+// ---- rebuild of the refinement map (regrid.cu)
+template <typename T>
+struct FlagArgs {
+    const T* u;           // the level's state
+    const int* nbr;       // its map
+    int n_groups;
+    int criterion;        // 0 density gradient, 1 pressure gradient, 2 density threshold
+    double threshold;
+    int n_buffer;         // flag buffer in cells, 0..8
+    double gamma;
+    unsigned* masks;      // [8 n_groups] output
+};
+template <typename T>
+cudaError_t launch_flag(const FlagArgs<T>& a, cudaStream_t st);
+
+template <typename T>
+struct RefineArgs {
+    const T* uc;          // parent level's state
+    const int* nbrc;      // parent level's map
+    int n_c;              // parent level's groups
+    const int* parent_new;// [n_new] parent patch of every new group
+    const int* inherit;   // [n_new] old group to copy, or -1: interpolate
+    const T* u_old;       // previous state of the rebuilt level (n_old groups), or nullptr
+    int n_old;
+    T* u_new;             // [5][8 n_new][512] output
+    int n_new;
+};
+template <typename T>
+cudaError_t launch_refine(const RefineArgs<T>& a, cudaStream_t st);
+
 // ---- diagnostics
 template <typename T>
 struct DiagLevel {
