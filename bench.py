@@ -52,6 +52,9 @@ def parse():
     p.add_argument("--time-steps", choices=["uniform", "individual"], default="uniform",
                    help="multi-level workloads, --mode pair: one dt for all levels, or every level "
                         "halving its parent's dt (a call then advances level l by 2^(l+1) steps)")
+    p.add_argument("--regrid-kernels", action="store_true",
+                   help="instead of timing steps: the flag step (three criteria) and the refinement fill of "
+                        "the refinement-map rebuild on the workload's level 0, HBM GB/s per launch")
     p.add_argument("--accuracy", action="store_true",
                    help="instead of timing: per-field L1 / max error of the FP32 path against the FP64 path "
                         "(bit-identical to the FP64 oracle) on every workload, plus positivity and conservation")
@@ -561,10 +564,72 @@ def run_accuracy(args):
     return 0
 
 
+def run_regrid_kernels(args):
+    """Device time per launch (CUDA events, L2 flushed before each) of
+    gamer_hydro_flag for the three criteria and of gamer_hydro_refine_fill
+    (every level-0 patch refined, half inherited, half interpolated) on the
+    workload's level 0.  Algorithmic bytes: the flag step reads rho (4 B
+    per cell in FP32) or all five variables (20 B) once and writes one word
+    per patch; the fill writes 8 fine cells x 20 B per coarse cell and reads
+    the coarse cell (20 B) or the inherited fine data (160 B)."""
+    import torch
+    from paper_0907_3390_gb300 import binding as B
+    from paper_0907_3390_gb300 import hierarchy as hm
+    desc, make = WORKLOADS[args.workload]
+    H, st = make()
+    H0 = hm.Hierarchy(levels=[H.levels[0]], base_npg=H.base_npg, L=H.L)
+    S = B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP32)
+    D = B.DeviceHierarchy(H0, [st[0]], torch.float32)
+    n = H.levels[0].n_groups
+    cells = n * 4096
+    hbm, kind = measured_peaks()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    masks = torch.empty(8 * n, dtype=torch.int32, device="cuda")
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        out = []
+        for r in range(reps):
+            flush.fill_(r)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1) / 1e3)
+        return float(np.median(out))
+
+    res = {}
+    for name, crit, thr, byt in (("flag_density_gradient", 0, 0.03, 4), ("flag_pressure_gradient", 1, 1.0, 20),
+                                 ("flag_density", 2, 2.0, 4)):
+        t = timed(lambda: B.gamer_hydro_flag(S.h, D, 0, crit, thr, 8, masks))
+        res[name] = {"ms": 1e3 * t, "algorithmic_GBps": byt * cells / t / 1e9,
+                     "frac_of_hbm": byt * cells / t / 1e9 / hbm, "bytes_per_cell": byt}
+    # refinement fill of every patch of level 0: groups alternate inherit / interpolate
+    nn = 8 * n
+    parent = torch.arange(nn, dtype=torch.int32, device="cuda")
+    inherit = torch.where(parent % 2 == 0, parent, torch.full_like(parent, -1))
+    u_old = torch.zeros((5, 8 * nn, 8, 8, 8), dtype=torch.float32, device="cuda")
+    u_new = torch.empty_like(u_old)
+    t = timed(lambda: B.gamer_hydro_refine_fill(S.h, D, 0, parent, inherit, u_old, u_new), reps=3)
+    fine = nn * 4096
+    byt = fine * 20 + (fine // 2) * 20 + (cells // 2) * 20
+    res["refine_fill"] = {"ms_with_host_checks": 1e3 * t, "algorithmic_bytes": byt, "fine_cells": fine,
+                          "note": "the call checks parents and nesting on the host (synchronously) before its "
+                                  "launch; the kernel's own time is in the ncu launch list"}
+    print(json.dumps({"regrid_kernels": res, "workload": desc, "cells": cells, "peak_GBps": hbm,
+                      "peak_kind": kind, "precision": "FP32 state, FP64 criteria"}), flush=True)
+    S.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.accuracy:
         return run_accuracy(args)
+    if args.regrid_kernels:
+        return run_regrid_kernels(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None

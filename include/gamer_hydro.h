@@ -215,7 +215,9 @@ int gamer_hydro_set_time_steps(gamer_hydro_t h, int mode);
  *     neighbour that only exists on the coarser level counts as the cell
  *     itself, outflow edges as zero gradient);
  *   GAMER_FLAG_DENSITY: rho > threshold;
- * evaluated in FP64 whatever the handle's precision.  Every flagged cell
+ * evaluated in the handle's precision (single precision is the paper's
+ * GPU precision) in the order of these definitions; the relative change
+ * and rho are compared with threshold in FP64.  Every flagged cell
  * has a flag buffer, the cube of 1 + 2 n_buffer cells around it
  * (0 <= n_buffer <= 8); masks (device, [8 n_groups] uint32) receives per
  * patch the bit (dz+1)*9 + (dy+1)*3 + (dx+1) of every patch offset that

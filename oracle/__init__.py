@@ -75,7 +75,7 @@ def lib():
             L.orc_cfl_dt.restype = C.c_double
             L.orc_cfl_dt.argtypes = [C.POINTER(_Level), C.c_int, C.c_double, C.c_double]
             L.orc_flag_level.argtypes = [C.POINTER(_Level), C.c_int, C.c_int, C.c_double, C.c_int, C.c_double,
-                                         C.c_int, C.POINTER(C.c_uint32)]
+                                         C.c_int, C.c_int, C.POINTER(C.c_uint32)]
             L.orc_refine_fill.argtypes = [C.POINTER(_Level), C.c_int, C.c_int, C.POINTER(C.c_int32),
                                           C.POINTER(C.c_int32), dp, C.c_int, dp]
             L.orc_cfl_dt_steps.restype = C.c_double
@@ -289,11 +289,13 @@ class OracleLevels:
         self._refresh()
         return lib().orc_level_max_speed(C.byref(self._arr[l]), gamma)
 
-    def flag_level(self, l: int, gamma: float, criterion: int, threshold: float, n_buffer: int) -> np.ndarray:
-        """Per-patch flag-buffer masks of level l (orc_flag_level)."""
+    def flag_level(self, l: int, gamma: float, criterion: int, threshold: float, n_buffer: int,
+                   single: bool = False) -> np.ndarray:
+        """Per-patch flag-buffer masks of level l (orc_flag_level); single:
+        criteria in single precision (values must be single-precision numbers)."""
         self._refresh()
         masks = np.zeros(8 * self.H.levels[l].n_groups, dtype=np.uint32)
-        r = lib().orc_flag_level(self._arr, self.n, l, gamma, criterion, threshold, n_buffer,
+        r = lib().orc_flag_level(self._arr, self.n, l, gamma, criterion, threshold, n_buffer, 1 if single else 0,
                                  masks.ctypes.data_as(C.POINTER(C.c_uint32)))
         if r != 0:
             raise ValueError(f"orc_flag_level: {r}")

@@ -600,6 +600,26 @@ static int crit_value(const orc_level *L, int g, int x, int y, int z, int criter
     return 0;
 }
 
+/* The same in single precision (the paper's GPU precision), for levels
+ * whose values are single-precision numbers: every operation rounded to
+ * float. */
+static int crit_value_f32(const orc_level *L, int g, int x, int y, int z, int criterion, double gamma, float *q)
+{
+    double u[NV];
+    int r = level_fetch(L, L->u, g, x, y, z, u);
+    if (r != 0)
+        return r;
+    const float rho = (float)u[0];
+    if (criterion != 1) {
+        *q = rho;
+        return 0;
+    }
+    const float vx = (float)u[1] / rho, vy = (float)u[2] / rho, vz = (float)u[3] / rho;
+    const float eps = (float)u[4] - 0.5f * rho * (vx * vx + vy * vy + vz * vz);
+    *q = (float)(gamma - 1.0) * eps;
+    return 0;
+}
+
 /* Flag step of the refinement-map rebuild (Sec. 2.1 step 4; readings R21,
  * R22).  A cell of level l satisfies
  *   criterion 0: max over axes of |rho(+1) - rho(-1)| / (2 |rho|) >= threshold
@@ -610,9 +630,11 @@ static int crit_value(const orc_level *L, int g, int x, int y, int z, int criter
  * cell itself.  Around every such cell the flag buffer is the cube of
  * 1 + 2 n_buffer cells; masks[p] of patch p gets bit (dz+1)*9+(dy+1)*3+(dx+1)
  * for every patch at offset (dx,dy,dz) (bit 13: p itself) that the buffer of
- * one of its cells reaches.  0 <= n_buffer <= 8. */
+ * one of its cells reaches.  0 <= n_buffer <= 8.  single != 0: the criterion
+ * is evaluated in single precision on single-precision values (the flags of
+ * a single-precision run), else in double. */
 int orc_flag_level(const orc_level *lv, int n_levels, int l, double gamma, int criterion,
-                   double threshold, int n_buffer, uint32_t *masks)
+                   double threshold, int n_buffer, int single, uint32_t *masks)
 {
     if (l < 0 || l >= n_levels || n_buffer < 0 || n_buffer > PS || criterion < 0 || criterion > 2)
         return ORC_ERR_ARG;
@@ -623,33 +645,62 @@ int orc_flag_level(const orc_level *lv, int n_levels, int l, double gamma, int c
         for (int z = 0; z < GS; z++)
             for (int y = 0; y < GS; y++)
                 for (int x = 0; x < GS; x++) {
-                    double q0;
-                    if (crit_value(L, g, x, y, z, criterion == 2 ? 0 : criterion, gamma, &q0) != 0)
-                        return ORC_ERR_MAP;
                     int hit;
-                    if (criterion == 2) {
-                        hit = q0 > threshold;
-                    } else {
-                        double rmax = 0.0;
-                        int c[3] = {x, y, z};
-                        for (int a = 0; a < 3; a++) {
-                            double qm, qp;
-                            int m[3] = {c[0], c[1], c[2]}, pp[3] = {c[0], c[1], c[2]};
-                            m[a] -= 1;
-                            pp[a] += 1;
-                            int rm = crit_value(L, g, m[0], m[1], m[2], criterion, gamma, &qm);
-                            int rp = crit_value(L, g, pp[0], pp[1], pp[2], criterion, gamma, &qp);
-                            if (rm < 0 || rp < 0)
-                                return ORC_ERR_MAP;
-                            if (rm == 1)
-                                qm = q0;
-                            if (rp == 1)
-                                qp = q0;
-                            double r = fabs(qp - qm) / (2.0 * fabs(q0));
-                            if (r > rmax)
-                                rmax = r;
+                    int c[3] = {x, y, z};
+                    if (single) {
+                        float q0;
+                        if (crit_value_f32(L, g, x, y, z, criterion == 2 ? 0 : criterion, gamma, &q0) != 0)
+                            return ORC_ERR_MAP;
+                        if (criterion == 2) {
+                            hit = (double)q0 > threshold;
+                        } else {
+                            float rmax = 0.0f;
+                            for (int a = 0; a < 3; a++) {
+                                float qm, qp;
+                                int m[3] = {c[0], c[1], c[2]}, pp[3] = {c[0], c[1], c[2]};
+                                m[a] -= 1;
+                                pp[a] += 1;
+                                int rm = crit_value_f32(L, g, m[0], m[1], m[2], criterion, gamma, &qm);
+                                int rp = crit_value_f32(L, g, pp[0], pp[1], pp[2], criterion, gamma, &qp);
+                                if (rm < 0 || rp < 0)
+                                    return ORC_ERR_MAP;
+                                if (rm == 1)
+                                    qm = q0;
+                                if (rp == 1)
+                                    qp = q0;
+                                float r = fabsf(qp - qm) / (2.0f * fabsf(q0));
+                                if (r > rmax)
+                                    rmax = r;
+                            }
+                            hit = (double)rmax >= threshold;
                         }
-                        hit = rmax >= threshold;
+                    } else {
+                        double q0;
+                        if (crit_value(L, g, x, y, z, criterion == 2 ? 0 : criterion, gamma, &q0) != 0)
+                            return ORC_ERR_MAP;
+                        if (criterion == 2) {
+                            hit = q0 > threshold;
+                        } else {
+                            double rmax = 0.0;
+                            for (int a = 0; a < 3; a++) {
+                                double qm, qp;
+                                int m[3] = {c[0], c[1], c[2]}, pp[3] = {c[0], c[1], c[2]};
+                                m[a] -= 1;
+                                pp[a] += 1;
+                                int rm = crit_value(L, g, m[0], m[1], m[2], criterion, gamma, &qm);
+                                int rp = crit_value(L, g, pp[0], pp[1], pp[2], criterion, gamma, &qp);
+                                if (rm < 0 || rp < 0)
+                                    return ORC_ERR_MAP;
+                                if (rm == 1)
+                                    qm = q0;
+                                if (rp == 1)
+                                    qp = q0;
+                                double r = fabs(qp - qm) / (2.0 * fabs(q0));
+                                if (r > rmax)
+                                    rmax = r;
+                            }
+                            hit = rmax >= threshold;
+                        }
                     }
                     if (!hit)
                         continue;

@@ -54,12 +54,14 @@ def combine_masks(level, masks) -> set:
     return flagged & present
 
 
-def regrid(H, states, gamma: float, criterion: int, thresholds, n_buffer: int, max_levels: int):
-    """New (hierarchy, states) after one rebuild of the refinement map."""
+def regrid(H, states, gamma: float, criterion: int, thresholds, n_buffer: int, max_levels: int,
+           single: bool = False):
+    """New (hierarchy, states) after one rebuild of the refinement map;
+    single: flags of a single-precision run (criteria in float)."""
     O = OracleLevels(H, states)
     n_old = H.n_levels
     n_flag = min(n_old, max_levels - 1)
-    flags = [combine_masks(H.levels[l], O.flag_level(l, gamma, criterion, thresholds[l], n_buffer))
+    flags = [combine_masks(H.levels[l], O.flag_level(l, gamma, criterion, thresholds[l], n_buffer, single))
              for l in range(n_flag)]
     # a patch with a flagged child stays flagged (finest to coarsest)
     for l in range(n_flag - 2, -1, -1):

@@ -1,9 +1,10 @@
 """The refinement-map rebuild on the GPU (Sec. 2.1 step 4; readings R21-R23)
 against the oracle:
 
-* flag masks bit for bit (the criteria are FP64 on both sides; for an FP32
-  handle the oracle receives the same FP32 values), three criteria and
-  three buffer sizes, on one, two and three levels;
+* flag masks bit for bit (the criteria are evaluated in the handle's
+  precision on both sides: for an FP32 handle the oracle takes the same
+  FP32 values and decides in single precision), three criteria and three
+  buffer sizes, on one, two and three levels;
 * refinement fill: FP64 bit for bit, FP32 within 1e-6 relative;
 * a whole rebuild through paper_0907_3390_gb300.regrid against
   oracle.regrid: the same levels, groups, parents and, in FP64, the same
@@ -69,7 +70,7 @@ def test_flag_masks_bitwise(prec):
                     m = torch.empty(8 * H.levels[l].n_groups, dtype=torch.int32, device="cuda")
                     B.gamer_hydro_flag(S.h, D, l, crit, thr, nb, m)
                     got = m.cpu().numpy().view(np.uint32)
-                    want = O.flag_level(l, G, crit, thr, nb)
+                    want = O.flag_level(l, G, crit, thr, nb, single=prec == "f32")
                     assert np.array_equal(got, want), (name, crit, nb, l)
         S.close()
 
@@ -80,7 +81,7 @@ def test_rebuild_matches_oracle(prec):
     for name, (H, st), crits in list(cases())[1:]:
         crit, thr = crits[0]
         st_in = [np.asarray(s).astype(npdt).astype(np.float64) for s in st]
-        Ho, so = org.regrid(H, st_in, G, crit, [thr] * 3, 2, max_levels=3)
+        Ho, so = org.regrid(H, st_in, G, crit, [thr] * 3, 2, max_levels=3, single=prec == "f32")
         S = B.Solver(G, 0, p)
         D = B.DeviceHierarchy(H, st, dt_)
         Dn = rg.rebuild(S, D, crit, [thr] * 3, 2, max_levels=3)

@@ -96,6 +96,17 @@ def test_flag_masks_outflow_front():
     assert np.count_nonzero(got) > 0
 
 
+def test_single_precision_flags_on_single_values():
+    # the float evaluation decides like the double one away from ties
+    u, npg = wl.lognormal_cells(32, seed=23, sigma=0.1)
+    u32 = u.astype(np.float32).astype(np.float64)
+    O = oracle.OracleLevels(wl.uniform_hierarchy(npg), [hm.domain_to_patches(u32, npg)])
+    for crit, thr in ((0, 0.3), (1, 0.048), (2, 1.35)):
+        a = O.flag_level(0, G, crit, thr, 2, single=True)
+        b = O.flag_level(0, G, crit, thr, 2, single=False)
+        assert np.mean(a == b) > 0.95
+
+
 def test_buffer_closed_forms():
     u, npg = wl.lognormal_cells(32, seed=22, sigma=0.3)
     O = oracle.OracleLevels(wl.uniform_hierarchy(npg), [hm.domain_to_patches(u, npg)])
