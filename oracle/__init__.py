@@ -78,6 +78,8 @@ def lib():
                                          C.c_int, C.c_int, C.POINTER(C.c_uint32)]
             L.orc_refine_fill.argtypes = [C.POINTER(_Level), C.c_int, C.c_int, C.POINTER(C.c_int32),
                                           C.POINTER(C.c_int32), dp, C.c_int, dp]
+            L.orc_sor_group.restype = C.c_int
+            L.orc_sor_group.argtypes = [dp, dp, C.c_double, C.c_double, C.c_int, C.c_double, dp]
             L.orc_cfl_dt_steps.restype = C.c_double
             L.orc_cfl_dt_steps.argtypes = [C.POINTER(_Level), C.c_int, C.c_double, C.c_double, C.c_int]
             L.orc_gather_block.argtypes = [C.POINTER(_Level), C.c_int, C.c_int, C.c_int, dp]
@@ -123,6 +125,16 @@ def tvd_column(q: np.ndarray, d: int, lam: float, gamma: float, limiter: int = V
     if r != 0:
         raise ValueError(f"orc_tvd_column: {r}")
     return out
+
+
+def sor_group(phi: np.ndarray, rho: np.ndarray, coef: float, omega: float, max_iter: int, tol: float):
+    """Red-black SOR of one patch group (orc_sor_group): returns (phi [18]^3
+    after the iterations, iterations done, last residual one-norm)."""
+    ph = np.array(phi, dtype=np.float64, order="C", copy=True).reshape(18, 18, 18)
+    rh = np.ascontiguousarray(rho, dtype=np.float64).reshape(16, 16, 16)
+    res = C.c_double(0.0)
+    it = lib().orc_sor_group(_dp(ph), _dp(rh), coef, omega, max_iter, tol, C.byref(res))
+    return ph, int(it), float(res.value)
 
 
 def minmod_children(block: np.ndarray) -> np.ndarray:

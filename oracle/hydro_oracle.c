@@ -768,6 +768,52 @@ int orc_refine_fill(const orc_level *lv, int l, int n_new, const int32_t *parent
     return ORC_OK;
 }
 
+/* ----------------------------------------------------- Poisson (SOR) */
+
+/* Red-black successive overrelaxation for one patch group (Sec. 2.3, Eqs.
+ * Residual and SOR; reading R24).  phi: [18][18][18] (x fastest) holding
+ * the Dirichlet ghost layer, which is kept, and the initial interior; rho:
+ * [16][16][16]; coef = 4 pi G dh^2.  One iteration updates the even
+ * interior cells (i + j + k even, interior indices 0..15) with
+ *   R = (phi(i+1) + phi(j+1) + phi(k+1) + phi(i-1) + phi(j-1) + phi(k-1)
+ *        - 6 phi) - coef rho,   phi <- phi + (omega / 6) R,
+ * and then the odd cells with the updated even values.  It stops after the
+ * iteration in which the one-norm of that iteration's residuals falls to
+ * tol times the one-norm of coef rho, or after max_iter iterations, and
+ * returns the number of iterations; *res gets the last residual norm. */
+int orc_sor_group(double *phi, const double *rho, double coef, double omega, int max_iter, double tol,
+                  double *res)
+{
+    const int P = GS + 2;
+    double src = 0.0;
+    for (int i = 0; i < GS * GS * GS; i++)
+        src += fabs(coef * rho[i]);
+    const double w6 = omega / 6.0;
+    double norm = 0.0;
+    int it = 0;
+    while (it < max_iter) {
+        norm = 0.0;
+        for (int color = 0; color < 2; color++)
+            for (int k = 0; k < GS; k++)
+                for (int j = 0; j < GS; j++)
+                    for (int i = 0; i < GS; i++) {
+                        if (((i + j + k) & 1) != color)
+                            continue;
+                        const int c = ((k + 1) * P + (j + 1)) * P + (i + 1);
+                        const double nb = ((((phi[c + 1] + phi[c + P]) + phi[c + P * P]) + phi[c - 1]) + phi[c - P]) +
+                                          phi[c - P * P];
+                        const double R = (nb - 6.0 * phi[c]) - coef * rho[(k * GS + j) * GS + i];
+                        phi[c] = phi[c] + w6 * R;
+                        norm += fabs(R);
+                    }
+        it++;
+        if (norm <= tol * src)
+            break;
+    }
+    *res = norm;
+    return it;
+}
+
 /* ------------------------------------------------------ CFL and checks */
 
 /* Largest signal speed c_s + max(|vx|,|vy|,|vz|) over all cells of level l
