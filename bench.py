@@ -55,6 +55,9 @@ def parse():
     p.add_argument("--regrid-kernels", action="store_true",
                    help="instead of timing steps: the flag step (three criteria) and the refinement fill of "
                         "the refinement-map rebuild on the workload's level 0, HBM GB/s per launch")
+    p.add_argument("--poisson", action="store_true",
+                   help="instead of timing steps: the red-black SOR Poisson solver on as many patch groups as "
+                        "the workload's level 0 (random potential and density, a fixed iteration count)")
     p.add_argument("--accuracy", action="store_true",
                    help="instead of timing: per-field L1 / max error of the FP32 path against the FP64 path "
                         "(bit-identical to the FP64 oracle) on every workload, plus positivity and conservation")
@@ -624,10 +627,55 @@ def run_regrid_kernels(args):
     return 0
 
 
+def run_poisson(args):
+    """gamer_poisson_sor on the workload's number of level-0 patch groups,
+    20 iterations (tol = 0), FP32 and FP64; cell-updates/s = 16^3 cells x
+    groups x iterations / device time (CUDA events, L2 flushed before).  The
+    block stays in shared memory for all iterations, so the bound is
+    shared-memory bandwidth: 7 reads + 1 write per cell update (32 B in FP32,
+    64 B in FP64) against SMs x 128 B per cycle x the max SM clock."""
+    import torch
+    from paper_0907_3390_gb300 import binding as B
+    desc, make = WORKLOADS[args.workload]
+    H, _ = make()
+    n = H.levels[0].n_groups
+    iters = 20
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    smem_peak = sms * 128 * 2070e6 / 1e9            # GB/s
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    out = {}
+    for name, prec, dt, b in (("fp32", B.GAMER_FP32, torch.float32, 32), ("fp64", B.GAMER_FP64, torch.float64, 64)):
+        phi0 = torch.randn((n, 18, 18, 18), generator=gen, device="cuda", dtype=dt)
+        rho = torch.randn((n, 16, 16, 16), generator=gen, device="cuda", dtype=dt)
+        phi = phi0.clone()
+        B.gamer_poisson_sor(prec, rho, phi, 0.5, 1.7, iters, 0.0)
+        times = []
+        for r in range(5):
+            phi.copy_(phi0)
+            flush.fill_(r)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            B.gamer_poisson_sor(prec, rho, phi, 0.5, 1.7, iters, 0.0)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        t = float(np.median(times))
+        upd = n * 4096 * iters
+        out[name] = {"ms": 1e3 * t, "cell_updates_per_s": upd / t, "smem_GBps": upd * b / t / 1e9,
+                     "smem_frac": upd * b / t / 1e9 / smem_peak}
+    print(json.dumps({"poisson_sor": out, "groups": n, "iterations": iters, "workload": desc,
+                      "smem_peak_GBps": smem_peak,
+                      "smem_peak_kind": f"derived: {sms} SMs x 128 B/cycle x 2070 MHz"}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.accuracy:
         return run_accuracy(args)
+    if args.poisson:
+        return run_poisson(args)
     if args.regrid_kernels:
         return run_regrid_kernels(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -240,6 +240,29 @@ int gamer_hydro_refine_fill(gamer_hydro_t h, const gamer_hierarchy_t *H, int lev
                             const int32_t *parent_new, const int32_t *inherit, const void *u_old, int n_old,
                             void *u_new);
 
+/* Red-black SOR Poisson solver of the refined levels (Sec. 2.3, Eqs.
+ * DiscretePoisson, Residual, SOR), one patch group per thread block, with
+ * no handle.  phi: device [n_groups][18][18][18] (x fastest), the 16^3
+ * interior's initial guess inside the Dirichlet ghost layer, which is kept;
+ * rho: device [n_groups][16][16][16]; coef = 4 pi G dh^2.  One iteration
+ * updates the even interior cells (i + j + k even, interior indices) by
+ *   R = (phi(i+1) + phi(j+1) + phi(k+1) + phi(i-1) + phi(j-1) + phi(k-1)
+ *        - 6 phi) - coef rho,   phi <- phi + (omega / 6) R
+ * and then the odd ones with the updated even values; a group stops after
+ * the iteration in which the one-norm of its residuals falls to tol times
+ * the one-norm of coef rho (tol = 0: never; the norms are then not
+ * formed at all, and otherwise summed in the data's precision per warp),
+ * or after max_iter iterations.  iters: device [n_groups] iteration counts, or NULL.
+ * precision: GAMER_FP32 or GAMER_FP64 (the data's type; FP64 follows the
+ * oracle's order of operations, so with tol = 0 it matches it bit for bit).
+ * 0 < omega < 2.  Work runs on cuda_stream (NULL: legacy stream),
+ * asynchronously.  The preparation of rho and of the ghost layer
+ * (interpolation from the coarser level) and the potential correction of
+ * the paper are not part of this call.  Errors: GAMER_ERR_ARG,
+ * GAMER_ERR_CUDA; message from gamer_hydro_last_error(NULL). */
+int gamer_poisson_sor(int precision, int n_groups, const void *rho, void *phi, double coef, double omega,
+                      int max_iter, double tol, int32_t *iters, void *cuda_stream);
+
 /* Result of the last gamer_hydro_step or gamer_hydro_step_pair: the dt it
  * used, the dt the next step will use, the leaf sums of u * dh^3 and the
  * bad-cell count of the new state.  Waits for that step.  Any output

@@ -28,7 +28,7 @@ EXPORTS = [
     "gamer_hydro_set_parity", "gamer_hydro_get_parity", "gamer_hydro_cfl_dt",
     "gamer_hydro_advance", "gamer_hydro_fixup", "gamer_hydro_advance_all",
     "gamer_hydro_check", "gamer_hydro_diagnose", "gamer_hydro_step", "gamer_hydro_step_pair",
-    "gamer_hydro_set_time_steps", "gamer_hydro_flag", "gamer_hydro_refine_fill",
+    "gamer_hydro_set_time_steps", "gamer_hydro_flag", "gamer_hydro_refine_fill", "gamer_poisson_sor",
     "gamer_hydro_step_result",
     "gamer_hydro_diagnose_noalloc", "gamer_hydro_tune", "gamer_hydro_get_config",
     "gamer_hydro_set_profiling", "gamer_hydro_last_error",
@@ -88,6 +88,8 @@ def load(build_if_needed: bool = True) -> C.CDLL:
         L.gamer_hydro_set_time_steps.argtypes = [H, C.c_int]
         L.gamer_hydro_flag.argtypes = [H, hp, C.c_int, C.c_int, C.c_double, C.c_int, vp]
         L.gamer_hydro_refine_fill.argtypes = [H, hp, C.c_int, C.c_int, vp, vp, vp, C.c_int, vp]
+        L.gamer_poisson_sor.argtypes = [C.c_int, C.c_int, vp, vp, C.c_double, C.c_double, C.c_int, C.c_double,
+                                        vp, vp]
         L.gamer_hydro_step_result.argtypes = [H, dp, dp, dp, C.POINTER(C.c_int64)]
         L.gamer_hydro_diagnose_noalloc.argtypes = [C.c_double, C.c_int, hp, C.c_double, vp, dp, dp,
                                                    C.POINTER(C.c_int64)]
@@ -191,6 +193,16 @@ def gamer_hydro_refine_fill(h, H, level: int, parent_new, inherit, u_old, u_new)
     n_old = 0 if u_old is None else int(u_old.shape[1]) // 8
     _check(h, load().gamer_hydro_refine_fill(h, H.struct(), level, n_new, parent_new.data_ptr(), inherit.data_ptr(),
                                               None if u_old is None else u_old.data_ptr(), n_old, u_new.data_ptr()))
+
+
+def gamer_poisson_sor(precision: int, rho, phi, coef: float, omega: float, max_iter: int, tol: float,
+                      iters=None, stream=None) -> None:
+    """rho: device tensor [n, 16, 16, 16]; phi: device tensor [n, 18, 18, 18]
+    (updated in place); iters: device int32 tensor [n] or None."""
+    n = int(rho.shape[0])
+    st = None if stream is None else getattr(stream, "cuda_stream", stream)
+    _check(None, load().gamer_poisson_sor(precision, n, rho.data_ptr(), phi.data_ptr(), coef, omega, max_iter, tol,
+                                          None if iters is None else iters.data_ptr(), st))
 
 
 def gamer_hydro_step_pair(h, H, cfl: float) -> None:

@@ -10,7 +10,9 @@ Each translation unit is compiled in parallel, then linked with
 * hydro_api.cu: host code of the C ABI;
 * noalloc.cu: the allocation-free diagnostics entry point;
 * regrid.cu: flag step and refinement fill of the refinement-map rebuild,
-  ``-fmad=false`` (FP64 criteria in their plain order).
+  ``-fmad=false`` (criteria in their plain order);
+* poisson.cu: red-black SOR Poisson solver of one patch group per block,
+  ``-fmad=false`` (FP64 in the oracle's order).
 """
 from __future__ import annotations
 
@@ -36,6 +38,7 @@ UNITS = {
     "hydro_api.cu": [],
     "noalloc.cu": [],
     "regrid.cu": ["-fmad=false"],
+    "poisson.cu": ["-fmad=false"],
 }
 
 
