@@ -779,8 +779,9 @@ int orc_refine_fill(const orc_level *lv, int l, int n_new, const int32_t *parent
  *        - 6 phi) - coef rho,   phi <- phi + (omega / 6) R,
  * and then the odd cells with the updated even values.  It stops after the
  * iteration in which the one-norm of that iteration's residuals falls to
- * tol times the one-norm of coef rho, or after max_iter iterations, and
- * returns the number of iterations; *res gets the last residual norm. */
+ * tol times the one-norm of coef rho, or after max_iter iterations (tol = 0
+ * asks for exactly max_iter iterations), and returns the number of
+ * iterations; *res gets the last residual norm. */
 int orc_sor_group(double *phi, const double *rho, double coef, double omega, int max_iter, double tol,
                   double *res)
 {
@@ -807,7 +808,7 @@ int orc_sor_group(double *phi, const double *rho, double coef, double omega, int
                         norm += fabs(R);
                     }
         it++;
-        if (norm <= tol * src)
+        if (tol > 0.0 && norm <= tol * src)
             break;
     }
     *res = norm;
