@@ -395,34 +395,36 @@ def run_extras(args, B, torch, H, st, cells, dev, stream, updates):
     # input state from pinned host memory, advances it through the same
     # call as the timed step (whose last kernel writes the step result to
     # mapped host memory) and copies the new state back to pinned host
-    # memory.  Two independent states are in flight (double buffering, one
-    # handle each): the copy-in of step k+1 (own stream) overlaps the
-    # compute of step k (the launch stream) and the copy-out of step k-1
-    # (own stream), as a serving loop over independent states would run.
+    # memory.  NB independent states are in flight (one handle each): the
+    # copy-in of step k+1 (own stream) overlaps the compute of step k (the
+    # launch stream) and the copy-out of step k-1 (own stream), as a serving
+    # loop over independent states would run; with three states a buffer's
+    # copy-out and its next copy-in do not hold up the step in between.
     sets = 2 if args.mode == "pair" else 1
     s_in = torch.cuda.Stream(device=dev)
     s_out = torch.cuda.Stream(device=dev)
-    solvers = [B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP32, stream=stream) for _ in range(2)]
+    NB = 3
+    solvers = [B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP32, stream=stream) for _ in range(NB)]
     if args.time_steps == "individual" and len(H.levels) > 1:
         for S in solvers:
             B.gamer_hydro_set_time_steps(S.h, B.GAMER_TIME_STEPS_INDIVIDUAL)
-    bufs = [B.DeviceHierarchy(H, st, torch.float32, device=dev) for _ in range(2)]
+    bufs = [B.DeviceHierarchy(H, st, torch.float32, device=dev) for _ in range(NB)]
     host_in = [x.cpu().pin_memory() for x in bufs[0].u]
-    host_out = [[torch.empty_like(x).pin_memory() for x in host_in] for _ in range(2)]
-    ev_in = [torch.cuda.Event() for _ in range(2)]
-    ev_step = [torch.cuda.Event() for _ in range(2)]
-    ev_out = [torch.cuda.Event() for _ in range(2)]
+    host_out = [[torch.empty_like(x).pin_memory() for x in host_in] for _ in range(NB)]
+    ev_in = [torch.cuda.Event() for _ in range(NB)]
+    ev_step = [torch.cuda.Event() for _ in range(NB)]
+    ev_out = [torch.cuda.Event() for _ in range(NB)]
     n_e2e = max(4, min(2 * args.steps, 20))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    warm = 4
+    warm = 2 * NB
     for it in range(warm + n_e2e):
         if it == warm:
             torch.cuda.synchronize()
             e0.record(stream)
             s_in.wait_stream(stream)             # the first timed copy-in starts after e0
-        b = it % 2
+        b = it % NB
         S, D = solvers[b], bufs[b]
-        if it >= 2:
+        if it >= NB:
             s_in.wait_event(ev_step[b])          # the previous step on this buffer is done with u
             s_in.wait_event(ev_out[b])           # and its result has been copied out
         with torch.cuda.stream(s_in):
@@ -430,7 +432,7 @@ def run_extras(args, B, torch, H, st, cells, dev, stream, updates):
                 D.u[l].copy_(host_in[l], non_blocking=True)
             ev_in[b].record(s_in)
         stream.wait_event(ev_in[b])
-        if it >= 2:
+        if it >= NB:
             stream.wait_event(ev_out[b])
         if sets == 2:
             B.gamer_hydro_step_pair(S.h, D, CFL)  # result back in u
@@ -444,8 +446,8 @@ def run_extras(args, B, torch, H, st, cells, dev, stream, updates):
             for l in range(len(D.u)):
                 host_out[b][l].copy_(res_bufs[l], non_blocking=True)
             ev_out[b].record(s_out)
-    stream.wait_event(ev_out[0])
-    stream.wait_event(ev_out[1])
+    for b in range(NB):
+        stream.wait_event(ev_out[b])
     e1.record(stream)
     torch.cuda.synchronize()
     for S in solvers:
@@ -454,7 +456,7 @@ def run_extras(args, B, torch, H, st, cells, dev, stream, updates):
     nbytes = sum(x.numel() * 4 for x in host_in)
     out["e2e"] = {"value": updates / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                   "d2h_bytes_per_step": nbytes + 88,      # + the step result (11 x 8 B)
-                  "pipeline": "2 independent states in flight; copy-in, step and copy-out on 3 streams"}
+                  "pipeline": f"{NB} independent states in flight; copy-in, step and copy-out on 3 streams"}
     for S in solvers:
         S.close()
 
@@ -622,7 +624,7 @@ def run_regrid_kernels(args):
                           "note": "the call checks parents and nesting on the host (synchronously) before its "
                                   "launch; the kernel's own time is in the ncu launch list"}
     print(json.dumps({"regrid_kernels": res, "workload": desc, "cells": cells, "peak_GBps": hbm,
-                      "peak_kind": kind, "precision": "FP32 state, FP64 criteria"}), flush=True)
+                      "peak_kind": kind, "precision": "FP32 state and criteria"}), flush=True)
     S.close()
     return 0
 
@@ -631,9 +633,10 @@ def run_poisson(args):
     """gamer_poisson_sor on the workload's number of level-0 patch groups,
     20 iterations (tol = 0), FP32 and FP64; cell-updates/s = 16^3 cells x
     groups x iterations / device time (CUDA events, L2 flushed before).  The
-    block stays in shared memory for all iterations, so the bound is
-    shared-memory bandwidth: 7 reads + 1 write per cell update (32 B in FP32,
-    64 B in FP64) against SMs x 128 B per cycle x the max SM clock."""
+    block stays in shared memory for all iterations and each thread keeps its
+    own x-row in registers, so the bound is shared-memory bandwidth: the four
+    y and z neighbours read and the new value written per cell update (20 B
+    in FP32, 40 B in FP64) against SMs x 128 B per cycle x the max SM clock."""
     import torch
     from paper_0907_3390_gb300 import binding as B
     desc, make = WORKLOADS[args.workload]
@@ -645,7 +648,7 @@ def run_poisson(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     gen = torch.Generator(device="cuda").manual_seed(7)
     out = {}
-    for name, prec, dt, b in (("fp32", B.GAMER_FP32, torch.float32, 32), ("fp64", B.GAMER_FP64, torch.float64, 64)):
+    for name, prec, dt, b in (("fp32", B.GAMER_FP32, torch.float32, 20), ("fp64", B.GAMER_FP64, torch.float64, 40)):
         phi0 = torch.randn((n, 18, 18, 18), generator=gen, device="cuda", dtype=dt)
         rho = torch.randn((n, 16, 16, 16), generator=gen, device="cuda", dtype=dt)
         phi = phi0.clone()

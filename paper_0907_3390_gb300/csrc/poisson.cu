@@ -3,10 +3,12 @@
 // patch group, the whole 18^3 potential block (16^3 interior + the
 // Dirichlet ghost layer) in shared memory for all iterations -- on GB300 it
 // fits with room to spare, where the paper had to split it between shared
-// memory and registers -- and each thread owning one interior x-row, whose
-// 8 even and 8 odd cells it updates in the two half-steps, with 4 pi G dh^2
-// rho of its 16 cells in registers.  Compiled with -fmad=false: the FP64
-// path evaluates Eqs. Residual and SOR in the oracle's order.
+// memory and registers.  Each thread owns one interior x-row: its 16 cells,
+// their two x-ghosts and 4 pi G dh^2 rho of the row stay in registers, so
+// an update reads only its four y and z neighbours from shared memory and
+// writes its new value back for the neighbouring rows.  Compiled with
+// -fmad=false: the FP64 path evaluates Eqs. Residual and SOR in the
+// oracle's order.
 #include <cstdint>
 #include <string>
 
@@ -15,80 +17,116 @@
 
 namespace gh {
 
-constexpr int PP = GS + 2;            // 18
+constexpr int PP = GS + 2;            // 18 cells per row of the block
+constexpr int PL = PP * PP + 1;       // plane pitch: odd, so that the four planes of a warp use disjoint banks
 constexpr int NT_SOR = 256;           // one thread per interior x-row
+constexpr int HR = GS / 2;            // cells of one colour in a row
 
-template <typename T>
+// One half-step of a thread's row: the cells with x parity I0 (warp-uniform,
+// the warps being grouped by the parity of j + k), in increasing x.  re/ro:
+// the row's even-x / odd-x cells; gl, gr: its x-ghosts; cre/cro: 4 pi G dh^2
+// rho of the even-x / odd-x cells.  The six neighbours are summed in the
+// order x+, y+, z+, x-, y-, z- (Eq. Residual), then phi += (omega/6) R (Eq.
+// SOR).
+template <int I0, bool CHECK, typename T>
+__device__ __forceinline__ void sor_half(T* __restrict__ s, int row, T (&re)[HR], T (&ro)[HR], T gl, T gr,
+                                         const T (&cre)[HR], const T (&cro)[HR], T w6, T& norm) {
+#pragma unroll
+    for (int q = 0; q < HR; ++q) {
+        const int c = row + I0 + 2 * q;
+        const T cur = I0 ? ro[q] : re[q];
+        const T xp = I0 ? (q + 1 < HR ? re[q + 1] : gr) : ro[q];
+        const T xm = I0 ? re[q] : (q > 0 ? ro[q - 1] : gl);
+        const T nb = ((((xp + s[c + PP]) + s[c + PL]) + xm) + s[c - PP]) + s[c - PL];
+        const T R = (nb - T(6) * cur) - (I0 ? cro[q] : cre[q]);
+        const T nv = cur + w6 * R;
+        if (I0) ro[q] = nv;
+        else re[q] = nv;
+        s[c] = nv;
+        if (CHECK) norm += fabs(R);
+    }
+}
+
+template <typename T, bool CHECK>
 __global__ void __launch_bounds__(NT_SOR) k_sor(const T* __restrict__ rho, T* __restrict__ phi, T coef,
                                                 T w6, int max_iter, double tol, int* iters) {
     extern __shared__ unsigned char sraw[];
-    T* s = reinterpret_cast<T*>(sraw);                         // [18][18][18]
+    T* s = reinterpret_cast<T*>(sraw);                         // [18 planes of PL][18][18]
     __shared__ double s_red[NT_SOR / 32];
     __shared__ int s_stop;
     const int g = blockIdx.x, t = threadIdx.x;
     T* gphi = phi + (size_t)g * PP * PP * PP;
-    for (int i = t; i < PP * PP * PP; i += NT_SOR) s[i] = gphi[i];
-    const int j = t % GS, k = t / GS;                          // this thread's row
-    T cre[GS / 2], cro[GS / 2];                                // even-x and odd-x cells of the row
-    double src = 0.0;
+    for (int i = t; i < PP * PP * PP; i += NT_SOR) s[(i / (PP * PP)) * PL + i % (PP * PP)] = gphi[i];
+    // rows with j + k even on warps 0..3, odd on warps 4..7
+    const int par = t >> 7, r = t & 127;
+    const int k = r >> 3, j = 2 * (r & 7) + ((k + par) & 1);
+    const int row = (k + 1) * PL + (j + 1) * PP + 1;           // cell (0, j, k) of the row
+    T cre[HR], cro[HR];
     const T* rrow = rho + ((size_t)g * GS + k) * GS * GS + j * GS;
 #pragma unroll
-    for (int q = 0; q < GS / 2; ++q) {
+    for (int q = 0; q < HR; ++q) {
         cre[q] = coef * rrow[2 * q];
         cro[q] = coef * rrow[2 * q + 1];
-        src += fabs((double)cre[q]);
-        src += fabs((double)cro[q]);
     }
-    // one-norm of the source, block-wide (order-independent within rounding)
-    for (int o = 16; o > 0; o >>= 1) src += __shfl_xor_sync(0xffffffffu, src, o);
-    if ((t & 31) == 0) s_red[t >> 5] = src;
-    __syncthreads();
     double src_all = 0.0;
-    for (int w = 0; w < NT_SOR / 32; ++w) src_all += s_red[w];
+    if (CHECK) {
+        // one-norm of the source, block-wide
+        T src = T(0);
+#pragma unroll
+        for (int q = 0; q < HR; ++q) src += fabs(cre[q]) + fabs(cro[q]);
+        for (int o = 16; o > 0; o >>= 1) src += __shfl_xor_sync(0xffffffffu, src, o);
+        if ((t & 31) == 0) s_red[t >> 5] = (double)src;
+    }
     __syncthreads();
-    const int row = ((k + 1) * PP + (j + 1)) * PP + 1;         // cell (0, j, k) of the row
-    const bool check = tol > 0.0;                              // tol = 0: no norms at all
+    if (CHECK) {
+        for (int w = 0; w < NT_SOR / 32; ++w) src_all += s_red[w];
+        __syncthreads();
+    }
+    T re[HR], ro[HR];
+#pragma unroll
+    for (int q = 0; q < HR; ++q) {
+        re[q] = s[row + 2 * q];
+        ro[q] = s[row + 2 * q + 1];
+    }
+    const T gl = s[row - 1], gr = s[row + GS];
     int it = 0;
     while (it < max_iter) {
         T norm = T(0);                                         // residual one-norm, in the data's precision
 #pragma unroll
         for (int color = 0; color < 2; ++color) {
-            const int i0 = (color + j + k) & 1;                // first x of this colour in the row
-#pragma unroll
-            for (int q = 0; q < GS / 2; ++q) {
-                const int i = i0 + 2 * q;
-                const int c = row + i;
-                const T nb = ((((s[c + 1] + s[c + PP]) + s[c + PP * PP]) + s[c - 1]) + s[c - PP]) + s[c - PP * PP];
-                const T R = (nb - T(6) * s[c]) - (i0 ? cro[q] : cre[q]);
-                s[c] = s[c] + w6 * R;
-                norm += fabs(R);
-            }
+            // x parity of this colour's cells: (i + j + k) & 1 == color
+            if (((color + par) & 1) == 0) sor_half<0, CHECK>(s, row, re, ro, gl, gr, cre, cro, w6, norm);
+            else sor_half<1, CHECK>(s, row, re, ro, gl, gr, cre, cro, w6, norm);
             __syncthreads();
         }
         ++it;
-        if (!check) continue;
-        for (int o = 16; o > 0; o >>= 1) norm += __shfl_xor_sync(0xffffffffu, norm, o);
-        if ((t & 31) == 0) s_red[t >> 5] = (double)norm;
-        __syncthreads();
-        if (t == 0) {
-            double n = 0.0;
-            for (int w = 0; w < NT_SOR / 32; ++w) n += s_red[w];
-            s_stop = n <= tol * src_all;
+        if (CHECK) {
+            for (int o = 16; o > 0; o >>= 1) norm += __shfl_xor_sync(0xffffffffu, norm, o);
+            if ((t & 31) == 0) s_red[t >> 5] = (double)norm;
+            __syncthreads();
+            if (t == 0) {
+                double n = 0.0;
+                for (int w = 0; w < NT_SOR / 32; ++w) n += s_red[w];
+                s_stop = n <= tol * src_all;
+            }
+            __syncthreads();
+            if (s_stop) break;
         }
-        __syncthreads();
-        if (s_stop) break;
     }
-    for (int i = t; i < PP * PP * PP; i += NT_SOR) gphi[i] = s[i];
+    for (int i = t; i < PP * PP * PP; i += NT_SOR) gphi[i] = s[(i / (PP * PP)) * PL + i % (PP * PP)];
     if (iters != nullptr && t == 0) iters[g] = it;
 }
 
 template <typename T>
 static cudaError_t launch_sor(int n, const T* rho, T* phi, double coef, double omega, int max_iter, double tol,
                               int* iters, cudaStream_t st) {
-    const size_t smem = sizeof(T) * PP * PP * PP;
-    cudaError_t e = cudaFuncSetAttribute(k_sor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sizeof(T) * PP * PL;
+    const bool check = tol > 0.0;                              // tol = 0: no norms at all
+    cudaError_t e = check ? cudaFuncSetAttribute(k_sor<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                          : cudaFuncSetAttribute(k_sor<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_sor<T><<<n, NT_SOR, smem, st>>>(rho, phi, (T)coef, (T)(omega / 6.0), max_iter, tol, iters);
+    if (check) k_sor<T, true><<<n, NT_SOR, smem, st>>>(rho, phi, (T)coef, (T)(omega / 6.0), max_iter, tol, iters);
+    else k_sor<T, false><<<n, NT_SOR, smem, st>>>(rho, phi, (T)coef, (T)(omega / 6.0), max_iter, tol, iters);
     return cudaGetLastError();
 }
 

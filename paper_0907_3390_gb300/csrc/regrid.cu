@@ -3,6 +3,8 @@
 // Compiled with -fmad=false: the criteria are evaluated in the order of
 // their plain definition, in the handle's precision, so that flags never
 // depend on contraction.
+#include <cmath>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -36,51 +38,59 @@ constexpr int HP = GS + 2;    // the group with one halo cell per side
 // threshold.  Its flag buffer, the cube of 1 + 2 n_buffer cells around it,
 // sets in its patch's mask the bit of every patch offset (dx,dy,dz) it
 // reaches: (dz+1)*9 + (dy+1)*3 + (dx+1).
-template <typename T>
-__global__ void __launch_bounds__(NT_FLAG) k_flag(const FlagArgs<T> a) {
+//
+// The threshold comparisons run in T against thresholds rounded on the host
+// so that they decide exactly as the comparison of the value widened to
+// double with the double threshold: x >= d iff x >= (the least T >= d), and
+// x > d iff x > (the greatest T <= d).  GB300's FP64 rate would otherwise
+// make two FP64 operations per cell the largest cost of the kernel.
+template <typename T, int CRIT>
+__global__ void __launch_bounds__(NT_FLAG) k_flag(const FlagArgs<T> a, const T thr_ge, const T thr_gt) {
     __shared__ T s_q[HP * HP * HP];
     __shared__ int s_src[27], s_mask[27];
     __shared__ unsigned s_m[8];
     const int g = blockIdx.x, t = threadIdx.x;
-    if (t < 27) region_entry(a.nbr, g, t, s_src, s_mask);
-    if (t < 8) s_m[t] = 0u;
-    __syncthreads();
     const size_t vs = (size_t)a.n_groups * 8 * 512;
     const T gm1 = T(a.gamma - 1.0);
-    const int crit = a.criterion == 2 ? 0 : a.criterion;
+    constexpr int QC = CRIT == 1 ? 1 : 0;              // quantity: pressure or density
     // the group's own cells, in memory order (coalesced): local index j =
-    // ((patch * 8 + z) * 8 + y) * 8 + x with patch = (pz * 2 + py) * 2 + px
+    // ((patch * 8 + z) * 8 + y) * 8 + x with patch = (pz * 2 + py) * 2 + px.
+    // All loads of a thread are issued before the first store, and before
+    // the region table's dependent loads, so that they overlap.
     const size_t base = (size_t)g * CELLS_PG;
-    for (int j = t; j < CELLS_PG; j += NT_FLAG) {
-        const int p = j >> 9, x = ((p & 1) << 3) | (j & 7), y = (((p >> 1) & 1) << 3) | ((j >> 3) & 7),
-                  z = ((p >> 2) << 3) | ((j >> 6) & 7);
-        s_q[((z + 1) * HP + (y + 1)) * HP + (x + 1)] = crit_q<T>(a.u, vs, base + j, crit, gm1);
-    }
-    // the one-cell halo through the region table (the gradient criteria only)
-    constexpr int NH = HP * HP * HP - CELLS_PG;
-    for (int k = t; k < (a.criterion == 2 ? 0 : NH); k += NT_FLAG) {
-        // k-th halo position: z = -1 and z = 16 planes, then per interior z
-        // the y = -1 and y = 16 rows, then per interior (y, z) the two x ends
-        int x, y, z;
-        if (k < 2 * HP * HP) {
-            z = k < HP * HP ? -1 : GS;
-            const int r = k % (HP * HP);
-            x = r % HP - 1;
-            y = r / HP - 1;
-        } else if (k < 2 * HP * HP + 2 * GS * HP) {
-            const int r = k - 2 * HP * HP;
-            z = r / (2 * HP);
-            y = (r % (2 * HP)) < HP ? -1 : GS;
-            x = r % HP - 1;
-        } else {
-            const int r = k - 2 * HP * HP - 2 * GS * HP;
-            z = r / (2 * GS);
-            y = (r % (2 * GS)) >> 1;
-            x = (r & 1) ? GS : -1;
+    {
+        T q[CELLS_PG / NT_FLAG];
+#pragma unroll
+        for (int k = 0; k < CELLS_PG / NT_FLAG; ++k) q[k] = crit_q<T>(a.u, vs, base + k * NT_FLAG + t, QC, gm1);
+        if (CRIT != 2 && t < 27) region_entry(a.nbr, g, t, s_src, s_mask);
+        if (t < 8) s_m[t] = 0u;
+#pragma unroll
+        for (int k = 0; k < CELLS_PG / NT_FLAG; ++k) {
+            const int j = k * NT_FLAG + t;
+            const int p = j >> 9, x = ((p & 1) << 3) | (j & 7), y = (((p >> 1) & 1) << 3) | ((j >> 3) & 7),
+                      z = ((p >> 2) << 3) | ((j >> 6) & 7);
+            s_q[((z + 1) * HP + (y + 1)) * HP + (x + 1)] = q[k];
         }
+    }
+    __syncthreads();
+    // the six face layers of the one-cell halo through the region table (the
+    // gradient criteria only; the edges and corners of the halo are never
+    // read).  A face cell whose region only exists on the coarser level
+    // takes the value of the adjacent cell of the group, which is the one
+    // cell that reads it: the neighbour then counts as the cell itself.
+    constexpr int NF = 6 * GS * GS;
+#pragma unroll
+    for (int k = t; k < (CRIT == 2 ? 0 : NF); k += NT_FLAG) {
+        const int f = k >> 8, ax = f >> 1, a0 = k & 15, a1 = (k >> 4) & 15;
+        const int e = (f & 1) ? GS : -1;                   // halo coordinate along ax
+        int x = ax == 0 ? e : a0;
+        int y = ax == 0 ? a0 : (ax == 1 ? e : a1);
+        int z = ax == 2 ? e : a1;
         const int idx = ((z + 1) * HP + (y + 1)) * HP + (x + 1);
+        const int st = ax == 0 ? 1 : ax == 1 ? HP : HP * HP;
+        const int inner = (f & 1) ? idx - st : idx + st;
         const int src = resolve(s_src, s_mask, x, y, z);
-        s_q[idx] = src < 0 ? T(0) : crit_q<T>(a.u, vs, cell_offset(src, x, y, z), crit, gm1);
+        s_q[idx] = src < 0 ? s_q[inner] : crit_q<T>(a.u, vs, cell_offset(src, x, y, z), QC, gm1);
     }
     __syncthreads();
     // cells in memory order: pass k covers patch k, so the masks of a pass
@@ -93,25 +103,18 @@ __global__ void __launch_bounds__(NT_FLAG) k_flag(const FlagArgs<T> a) {
         const int c0 = ((z + 1) * HP + (y + 1)) * HP + (x + 1);
         const T q0 = s_q[c0];
         bool hit;
-        if (a.criterion == 2) {
-            hit = (double)q0 > a.threshold;
+        if (CRIT == 2) {
+            hit = q0 > thr_gt;
         } else {
-            T rmax = T(0);
-#pragma unroll
-            for (int ax = 0; ax < 3; ++ax) {
-                const int st = ax == 0 ? 1 : ax == 1 ? HP : HP * HP;
-                T q[2];
-#pragma unroll
-                for (int sd = 0; sd < 2; ++sd) {
-                    int c[3] = {x, y, z};
-                    c[ax] += sd == 0 ? -1 : 1;
-                    const int r = (region_of(c[2]) + 1) * 9 + (region_of(c[1]) + 1) * 3 + (region_of(c[0]) + 1);
-                    q[sd] = s_src[r] < 0 ? q0 : s_q[c0 + (sd == 0 ? -st : st)];
-                }
-                const T r = fabs(q[1] - q[0]) / (T(2) * fabs(q0));
-                if (r > rmax) rmax = r;
-            }
-            hit = (double)rmax >= a.threshold;
+            // max over the axes of |q(+1) - q(-1)| / (2 |q|), ignoring NaN
+            // ratios and starting from 0: the largest difference divided
+            // once gives the same value, division by one denominator being
+            // monotonic
+            T n = fabs(s_q[c0 + 1] - s_q[c0 - 1]);
+            n = fmax(n, fabs(s_q[c0 + HP] - s_q[c0 - HP]));
+            n = fmax(n, fabs(s_q[c0 + HP * HP] - s_q[c0 - HP * HP]));
+            const T r = n / (T(2) * fabs(q0));
+            hit = (r > T(0) ? r : T(0)) >= thr_ge;
         }
         unsigned m = 0u;
         if (hit) {
@@ -134,10 +137,28 @@ __global__ void __launch_bounds__(NT_FLAG) k_flag(const FlagArgs<T> a) {
     if (t < 8) a.masks[8 * g + t] = s_m[t];
 }
 
+// The least T >= d and the greatest T <= d (NaN stays NaN, so that every
+// comparison with it is false, as with d).
+template <typename T>
+static T round_up_to(double d) {
+    if (sizeof(T) == sizeof(double)) return (T)d;
+    const float f = (float)d;
+    return (double)f < d ? nextafterf(f, INFINITY) : f;
+}
+template <typename T>
+static T round_down_to(double d) {
+    if (sizeof(T) == sizeof(double)) return (T)d;
+    const float f = (float)d;
+    return (double)f > d ? nextafterf(f, -INFINITY) : f;
+}
+
 template <typename T>
 cudaError_t launch_flag(const FlagArgs<T>& a, cudaStream_t st) {
     if (a.n_groups <= 0) return cudaSuccess;
-    k_flag<T><<<a.n_groups, NT_FLAG, 0, st>>>(a);
+    const T ge = round_up_to<T>(a.threshold), gt = round_down_to<T>(a.threshold);
+    if (a.criterion == 0) k_flag<T, 0><<<a.n_groups, NT_FLAG, 0, st>>>(a, ge, gt);
+    else if (a.criterion == 1) k_flag<T, 1><<<a.n_groups, NT_FLAG, 0, st>>>(a, ge, gt);
+    else k_flag<T, 2><<<a.n_groups, NT_FLAG, 0, st>>>(a, ge, gt);
     return cudaGetLastError();
 }
 template cudaError_t launch_flag<float>(const FlagArgs<float>&, cudaStream_t);
@@ -146,8 +167,12 @@ template cudaError_t launch_flag<double>(const FlagArgs<double>&, cudaStream_t);
 constexpr int NT_REF = 256;
 
 // One block per group of the rebuilt level: a copy of the old group it
-// inherits, or every cell by Min-Mod interpolation from its parent patch
-// on the level below (the refinement step of Sec. 2.1).
+// inherits, or Min-Mod interpolation from its parent patch on the level
+// below (the refinement step of Sec. 2.1).  Interpolation runs per coarse
+// cell: a thread reads the cell and its six neighbours (through the coarse
+// region table) once, forms the three limited slopes of each variable and
+// writes all eight children, each as U + (sx Sx + sy Sy + sz Sz) / 4 in that
+// order, the children of one x-pair as one paired store.
 template <typename T>
 __global__ void __launch_bounds__(NT_REF) k_refine(const RefineArgs<T> a) {
     __shared__ int s_csrc[27], s_cmask[27];
@@ -155,12 +180,28 @@ __global__ void __launch_bounds__(NT_REF) k_refine(const RefineArgs<T> a) {
     const size_t vs = (size_t)a.n_new * 8 * 512;
     const int src = a.inherit[g];
     if (src >= 0) {
+        // copy in chunks of VB variables, every load of a chunk issued before
+        // its stores (all five variables at once in single precision)
+        constexpr int N4 = CELLS_PG * (int)sizeof(T) / 16;
+        constexpr int PER = N4 / NT_REF;
+        constexpr int VB = sizeof(T) == 4 ? NV : 1;
         const size_t vso = (size_t)a.n_old * 8 * 512;
-        for (int v = 0; v < NV; ++v) {
-            const float4* in = reinterpret_cast<const float4*>(a.u_old + v * vso + (size_t)src * CELLS_PG);
-            float4* out = reinterpret_cast<float4*>(a.u_new + v * vs + (size_t)g * CELLS_PG);
-            constexpr int N4 = CELLS_PG * (int)sizeof(T) / 16;
-            for (int i = t; i < N4; i += NT_REF) out[i] = in[i];
+#pragma unroll 1
+        for (int v0 = 0; v0 < NV; v0 += VB) {
+            float4 buf[VB][PER];
+#pragma unroll
+            for (int v = 0; v < VB; ++v) {
+                const float4* in =
+                    reinterpret_cast<const float4*>(a.u_old + (v0 + v) * vso + (size_t)src * CELLS_PG);
+#pragma unroll
+                for (int i = 0; i < PER; ++i) buf[v][i] = __ldcs(in + i * NT_REF + t);
+            }
+#pragma unroll
+            for (int v = 0; v < VB; ++v) {
+                float4* out = reinterpret_cast<float4*>(a.u_new + (v0 + v) * vs + (size_t)g * CELLS_PG);
+#pragma unroll
+                for (int i = 0; i < PER; ++i) __stcs(out + i * NT_REF + t, buf[v][i]);
+            }
         }
         return;
     }
@@ -168,13 +209,54 @@ __global__ void __launch_bounds__(NT_REF) k_refine(const RefineArgs<T> a) {
     if (t < 27) region_entry(a.nbrc, P >> 3, t, s_csrc, s_cmask);
     __syncthreads();
     const size_t vsc = (size_t)a.n_c * 8 * 512;
-    for (int i = t; i < CELLS_PG; i += NT_REF) {
-        const int x = i % GS, y = (i / GS) % GS, z = i / (GS * GS);
-        T val[NV];
-        prolong<T>(a.uc, nullptr, T(0), vsc, s_csrc, s_cmask, P & 1, (P >> 1) & 1, (P >> 2) & 1, x, y, z, val);
-        const size_t off = cell_offset(g, x, y, z);
+    const int px = P & 1, py = (P >> 1) & 1, pz = (P >> 2) & 1;
+    constexpr int dd[7][3] = {{0, 0, 0}, {-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+#pragma unroll 1
+    for (int i = t; i < PS * PS * PS; i += NT_REF) {
+        // coarse cell (i % 8, i / 8 % 8, i / 64) of the parent patch
+        const int ix = i & 7, iy = (i >> 3) & 7, iz = i >> 6;
+        const int cx = PS * px + ix, cy = PS * py + iy, cz = PS * pz + iz;
+        size_t off[7];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) a.u_new[v * vs + off] = val[v];
+        for (int q = 0; q < 7; ++q) {
+            int xa = cx + dd[q][0], ya = cy + dd[q][1], za = cz + dd[q][2];
+            const int s = resolve(s_csrc, s_cmask, xa, ya, za);
+            off[q] = cell_offset(s < 0 ? 0 : s, xa, ya, za);   // s < 0 cannot pass host validation
+        }
+        T c[NV][7];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int q = 0; q < 7; ++q) c[v][q] = a.uc[v * vsc + off[q]];
+        // children (2 ix + dx, 2 iy + dy, 2 iz + dz) of the new group
+        const size_t o0 = cell_offset(g, 2 * ix, 2 * iy, 2 * iz);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const T U = c[v][0];
+            const T Sx = minmod_slope(c[v][1], U, c[v][2]);
+            const T Sy = minmod_slope(c[v][3], U, c[v][4]);
+            const T Sz = minmod_slope(c[v][5], U, c[v][6]);
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+                for (int dy = 0; dy < 2; ++dy) {
+                    const T sy = dy ? T(1) : T(-1), sz = dz ? T(1) : T(-1);
+                    const T lo = U + T(0.25) * ((T(-1) * Sx + sy * Sy) + sz * Sz);
+                    const T hi = U + T(0.25) * ((T(1) * Sx + sy * Sy) + sz * Sz);
+                    T* o = a.u_new + v * vs + o0 + dz * 64 + dy * 8;
+                    if (sizeof(T) == 4) {
+                        float2 w;
+                        w.x = (float)lo;
+                        w.y = (float)hi;
+                        __stcs(reinterpret_cast<float2*>(o), w);
+                    } else {
+                        double2 w;
+                        w.x = (double)lo;
+                        w.y = (double)hi;
+                        __stcs(reinterpret_cast<double2*>(o), w);
+                    }
+                }
+        }
     }
 }
 

@@ -76,6 +76,39 @@ def test_flag_masks_bitwise(prec):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_flag_threshold_at_representable_boundary(prec):
+    """Thresholds equal to the largest criterion value and one double away on
+    either side: the kernel compares in the handle's precision against
+    thresholds rounded on the host, and must decide as the oracle, which
+    widens the value to double (R21)."""
+    p, dt_, npdt = PREC[prec]
+    u, npg = wl.lognormal_cells(32, seed=21, sigma=0.1)
+    H, st = wl.single_level(u, npg)
+    S = B.Solver(G, 0, p)
+    D = B.DeviceHierarchy(H, st, dt_)
+    O = oracle.OracleLevels(H, [np.asarray(x).astype(npdt).astype(np.float64) for x in st])
+    rho = u[0].astype(npdt)
+    # largest relative density change over one cell width, periodic domain,
+    # in the handle's precision and in the order of the criterion
+    two = npdt(2)
+    gmax = max(float(np.max(np.abs(np.roll(rho, -1, a) - np.roll(rho, 1, a)) / (two * np.abs(rho))))
+               for a in range(3))
+    m = torch.empty(8 * H.levels[0].n_groups, dtype=torch.int32, device="cuda")
+    n_flagged = {}
+    for crit, top in ((0, gmax), (2, float(rho.max()))):
+        for name, thr in (("below", np.nextafter(top, -np.inf)), ("at", top), ("above", np.nextafter(top, np.inf))):
+            B.gamer_hydro_flag(S.h, D, 0, crit, thr, 0, m)
+            got = m.cpu().numpy().view(np.uint32)
+            want = O.flag_level(0, G, crit, thr, 0, single=prec == "f32")
+            assert np.array_equal(got, want), (crit, name)
+            n_flagged[(crit, name)] = int(np.count_nonzero(got))
+    # the boundary cases are the ones that decide: >= for the gradient, > for the threshold
+    assert n_flagged[(0, "below")] >= 1 and n_flagged[(0, "at")] >= 1 and n_flagged[(0, "above")] == 0
+    assert n_flagged[(2, "below")] >= 1 and n_flagged[(2, "at")] == 0 and n_flagged[(2, "above")] == 0
+    S.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
 def test_rebuild_matches_oracle(prec):
     p, dt_, npdt = PREC[prec]
     for name, (H, st), crits in list(cases())[1:]:
