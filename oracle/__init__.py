@@ -78,6 +78,7 @@ def lib():
                                          C.c_int, C.c_int, C.POINTER(C.c_uint32)]
             L.orc_refine_fill.argtypes = [C.POINTER(_Level), C.c_int, C.c_int, C.POINTER(C.c_int32),
                                           C.POINTER(C.c_int32), dp, C.c_int, dp]
+            L.orc_gravity_level.argtypes = [dp, C.c_int, dp, C.c_double, C.c_double]
             L.orc_sor_group.restype = C.c_int
             L.orc_sor_group.argtypes = [dp, dp, C.c_double, C.c_double, C.c_int, C.c_double, dp]
             L.orc_cfl_dt_steps.restype = C.c_double
@@ -135,6 +136,17 @@ def sor_group(phi: np.ndarray, rho: np.ndarray, coef: float, omega: float, max_i
     res = C.c_double(0.0)
     it = lib().orc_sor_group(_dp(ph), _dp(rh), coef, omega, max_iter, tol, C.byref(res))
     return ph, int(it), float(res.value)
+
+
+def gravity_level(u: np.ndarray, phi: np.ndarray, dh: float, dt: float) -> np.ndarray:
+    """The gravity operator G over dt (orc_gravity_level) on one level's
+    state u [5][8 n][8][8][8] with the groups' potentials phi [n][18][18][18];
+    returns the new state."""
+    out = np.array(u, dtype=np.float64, order="C", copy=True)
+    n = out.shape[1] // 8
+    ph = np.ascontiguousarray(phi, dtype=np.float64).reshape(n, 18, 18, 18)
+    lib().orc_gravity_level(_dp(out), n, _dp(ph), dh, dt)
+    return out
 
 
 def minmod_children(block: np.ndarray) -> np.ndarray:
@@ -232,6 +244,11 @@ class OracleLevels:
         if r != 0:
             raise ValueError(f"orc_gather_block: {r}")
         return out
+
+    def gravity(self, l: int, phi: np.ndarray, dt: float) -> None:
+        """The gravity operator G over dt on level l's state, in place
+        (orc_gravity_level; phi [n_groups][18][18][18])."""
+        self.u[l][...] = gravity_level(self.u[l], phi, self.H.levels[l].dh, dt)
 
     def fixup_level(self, l: int, dt: float) -> None:
         self._refresh()

@@ -815,6 +815,53 @@ int orc_sor_group(double *phi, const double *rho, double coef, double omega, int
     return it;
 }
 
+/* ------------------------------------------------------- gravity (G) */
+
+/* The gravity operator G of the split scheme (Sec. 2.3: Eqs. MomConserve
+ * and EnergyConserve with their flux terms dropped; reading R25), over dt,
+ * on one level.  u: [5][8 n_groups][8][8][8], updated in place; phi:
+ * [n_groups][18][18][18] (x fastest), the potential of each patch group
+ * with one layer of ghost cells.  Per cell, along each axis k the 3-point
+ * central difference gives d_k = (phi(-1) - phi(+1)) lam = g_k dt with
+ * lam = dt / (2 dh); then
+ *   m_k <- m_k + rho d_k                                   (k = x, y, z)
+ *   e   <- e + 0.5 (((m_x + m'_x) d_x + (m_y + m'_y) d_y) + (m_z + m'_z) d_z)
+ * with m' the new momentum.  Over the step rho and g are constant, so this
+ * is the exact solution of the split equations; it changes the kinetic
+ * energy only, never the thermal energy. */
+void orc_gravity_level(double *u, int n_groups, const double *phi, double dh, double dt)
+{
+    const int P = GS + 2;
+    const double lam = dt / (2.0 * dh);
+    orc_level L;
+    memset(&L, 0, sizeof(L));
+    L.n_groups = n_groups;
+#pragma omp parallel for schedule(static)
+    for (int g = 0; g < n_groups; g++) {
+        const double *ph = phi + (size_t)g * P * P * P;
+        for (int z = 0; z < GS; z++)
+            for (int y = 0; y < GS; y++)
+                for (int x = 0; x < GS; x++) {
+                    const int c = ((z + 1) * P + (y + 1)) * P + (x + 1);
+                    const int st[3] = {1, P, P * P};
+                    size_t off[NV];
+                    for (int v = 0; v < NV; v++)
+                        off[v] = cell_index(&L, g, v, x, y, z);
+                    const double rho = u[off[0]];
+                    double d[3], m0[3], m1[3];
+                    for (int k = 0; k < 3; k++) {
+                        d[k] = (ph[c - st[k]] - ph[c + st[k]]) * lam;
+                        m0[k] = u[off[1 + k]];
+                        m1[k] = m0[k] + rho * d[k];
+                    }
+                    const double de = ((m0[0] + m1[0]) * d[0] + (m0[1] + m1[1]) * d[1]) + (m0[2] + m1[2]) * d[2];
+                    for (int k = 0; k < 3; k++)
+                        u[off[1 + k]] = m1[k];
+                    u[off[4]] = u[off[4]] + 0.5 * de;
+                }
+    }
+}
+
 /* ------------------------------------------------------ CFL and checks */
 
 /* Largest signal speed c_s + max(|vx|,|vy|,|vz|) over all cells of level l

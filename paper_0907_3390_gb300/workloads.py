@@ -313,3 +313,34 @@ def single_level(u_domain: np.ndarray, npg, L: float = 1.0, bc=("periodic",) * 3
     """Hierarchy + patch-layout state of a one-level domain array."""
     H = uniform_hierarchy(npg, L=L, bc=bc)
     return H, [domain_to_patches(u_domain, npg)]
+
+
+# ------------------------------------------------------------ potentials
+
+def potential_blocks(phi_fn, npg, dh: float) -> np.ndarray:
+    """[n_groups][18][18][18] potential blocks of a one-level domain of
+    (nx, ny, nz) patch groups: phi_fn(x, y, z) evaluated at the cell centres
+    of every group and of its one-cell ghost layer, x fastest, groups in the
+    order g = (gz ny + gy) nx + gx.  phi_fn is any callable on arrays (an
+    external potential or a test field)."""
+    nx, ny, nz = npg
+    i = np.arange(GROUP + 2, dtype=np.float64) - 0.5          # ghost centre at -0.5 dh
+    out = np.empty((nx * ny * nz, GROUP + 2, GROUP + 2, GROUP + 2))
+    for g in range(nx * ny * nz):
+        gx, gy, gz = g % nx, (g // nx) % ny, g // (nx * ny)
+        z, y, x = np.meshgrid((gz * GROUP + i) * dh, (gy * GROUP + i) * dh, (gx * GROUP + i) * dh, indexing="ij")
+        out[g] = phi_fn(x, y, z)
+    return out
+
+
+def periodic_potential_blocks(phi: np.ndarray, npg) -> np.ndarray:
+    """[n_groups][18][18][18] blocks cut from a periodic [nz][ny][nx] cell
+    array (ghost layer wrapped), groups in the order g = (gz ny + gy) nx + gx."""
+    nx, ny, nz = npg
+    p = np.pad(phi, 1, mode="wrap")
+    out = np.empty((nx * ny * nz, GROUP + 2, GROUP + 2, GROUP + 2), dtype=phi.dtype)
+    for g in range(nx * ny * nz):
+        gx, gy, gz = g % nx, (g // nx) % ny, g // (nx * ny)
+        out[g] = p[gz * GROUP:gz * GROUP + GROUP + 2, gy * GROUP:gy * GROUP + GROUP + 2,
+                   gx * GROUP:gx * GROUP + GROUP + 2]
+    return out
