@@ -58,6 +58,9 @@ def parse():
     p.add_argument("--poisson", action="store_true",
                    help="instead of timing steps: the red-black SOR Poisson solver on as many patch groups as "
                         "the workload's level 0 (random potential and density, a fixed iteration count)")
+    p.add_argument("--gravity", action="store_true",
+                   help="instead of timing steps: the gravity operator G on the workload's level 0 (HBM GB/s "
+                        "per launch, FP32 and FP64) and one xyzGGzyx double step against the fused pair step")
     p.add_argument("--accuracy", action="store_true",
                    help="instead of timing: per-field L1 / max error of the FP32 path against the FP64 path "
                         "(bit-identical to the FP64 oracle) on every workload, plus positivity and conservation")
@@ -673,12 +676,86 @@ def run_poisson(args):
     return 0
 
 
+def run_gravity(args):
+    """gamer_gravity_update on the workload's level 0 in a smooth periodic
+    potential, FP32 and FP64 (CUDA events, L2 flushed before each launch).
+    Algorithmic bytes per cell: the state read (5 values), momentum and
+    energy written (4 values) and the group's potential block once (18^3 /
+    16^3 values): 41.7 B in FP32, 83.4 B in FP64.  Then one xyzGGzyx double
+    step in FP32 (xyz set, G of twice the step, zyx set: three graph or
+    kernel launches) against the fused pair step on the same state, both as
+    cell-updates/s (2 per cell)."""
+    import torch
+    from paper_0907_3390_gb300 import binding as B
+    from paper_0907_3390_gb300 import workloads as W
+    desc, make = WORKLOADS[args.workload]
+    H, st = make()
+    lv = H.levels[0]
+    n, dh = lv.n_groups, lv.dh
+    cells = n * 4096
+    npg = H.base_npg
+    hbm, kind = measured_peaks()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    nd = npg[0] * 16
+    kx = 2 * np.pi * np.arange(nd) / nd
+    field = 0.01 * (np.sin(kx)[None, None, :] + np.cos(2 * kx)[None, :, None] + np.sin(3 * kx)[:, None, None])
+    phi_h = W.periodic_potential_blocks(field, npg)
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        out = []
+        for r in range(reps):
+            flush.fill_(r)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1) / 1e3)
+        return float(np.median(out))
+
+    res = {}
+    for name, prec, tdt, b in (("fp32", B.GAMER_FP32, torch.float32, 4), ("fp64", B.GAMER_FP64, torch.float64, 8)):
+        u = torch.tensor(np.asarray(st[0]), dtype=tdt, device="cuda")
+        phi = torch.tensor(phi_h, dtype=tdt, device="cuda")
+        t = timed(lambda: B.gamer_gravity_update(prec, u, phi, dh, 1e-4))
+        byt = cells * b * 9 + n * 18 ** 3 * b
+        res["gravity_" + name] = {"ms": 1e3 * t, "bytes_per_cell": byt / cells, "GBps": byt / t / 1e9,
+                                  "frac_of_hbm": byt / t / 1e9 / hbm}
+    # coupled double step against the pair step, FP32
+    S = B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP32)
+    D = B.DeviceHierarchy(H, st, torch.float32)
+    phi = torch.tensor(phi_h, dtype=torch.float32, device="cuda")
+    dt = B.gamer_hydro_cfl_dt(S.h, D, CFL)
+
+    def coupled():
+        S.step(D, dt)
+        B.gamer_gravity_update(B.GAMER_FP32, D.u[0], phi, dh, 2 * dt)
+        S.step(D, dt)
+    t_c = timed(coupled)
+    S.close()
+    S2 = B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP32)
+    D2 = B.DeviceHierarchy(H, st, torch.float32)
+    t_p = timed(lambda: B.gamer_hydro_step_pair(S2.h, D2, CFL))
+    S2.close()
+    res["xyzGGzyx_fp32"] = {"ms": 1e3 * t_c, "cell_updates_per_s": 2 * cells / t_c,
+                            "calls": "gamer_hydro_step (xyz), gamer_gravity_update (2 dt), gamer_hydro_step (zyx)"}
+    res["pair_fp32"] = {"ms": 1e3 * t_p, "cell_updates_per_s": 2 * cells / t_p,
+                        "calls": "gamer_hydro_step_pair (xyz + zyx in one launch, no gravity)"}
+    print(json.dumps({"gravity": res, "workload": desc, "cells": cells, "peak_GBps": hbm, "peak_kind": kind}),
+          flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.accuracy:
         return run_accuracy(args)
     if args.poisson:
         return run_poisson(args)
+    if args.gravity:
+        return run_gravity(args)
     if args.regrid_kernels:
         return run_regrid_kernels(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))

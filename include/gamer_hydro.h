@@ -263,6 +263,27 @@ int gamer_hydro_refine_fill(gamer_hydro_t h, const gamer_hierarchy_t *H, int lev
 int gamer_poisson_sor(int precision, int n_groups, const void *rho, void *phi, double coef, double omega,
                       int max_iter, double tol, int32_t *iters, void *cuda_stream);
 
+/* Gravity operator G of the split scheme (Sec. 2.3): the gravity source
+ * terms of Eqs. MomConserve and EnergyConserve, without the flux terms,
+ * applied to one level for a time dt, with no handle.  The hydro sweeps and
+ * G alternate as xyzGGzyx, the two G of a double step taken as one call
+ * with twice the hydro dt.  u: device [5][8 n_groups][8][8][8] (the level
+ * storage), updated in place; phi: device [n_groups][18][18][18] (x
+ * fastest), each group's potential with one ghost layer (the layout
+ * gamer_poisson_sor works on).  Per cell and axis k,
+ *   d_k = (phi(-1) - phi(+1)) * (dt / (2 dh))       (3-point difference: g_k dt)
+ *   m_k <- m_k + rho d_k
+ *   e   <- e + 0.5 (((m_x + m'_x) d_x + (m_y + m'_y) d_y) + (m_z + m'_z) d_z)
+ * with m' the new momentum (the exact solution over dt with rho and g
+ * fixed: the thermal energy does not change).  precision: GAMER_FP32 or
+ * GAMER_FP64 (the type of u and phi; FP64 follows the oracle's order of
+ * operations and matches it bit for bit).  dh > 0, dt >= 0, both finite.
+ * Work runs on cuda_stream (NULL: legacy stream), asynchronously.  Errors:
+ * GAMER_ERR_ARG (checked before any CUDA call), GAMER_ERR_CUDA; message
+ * from gamer_hydro_last_error(NULL). */
+int gamer_gravity_update(int precision, int n_groups, void *u, const void *phi, double dh, double dt,
+                         void *cuda_stream);
+
 /* Result of the last gamer_hydro_step or gamer_hydro_step_pair: the dt it
  * used, the dt the next step will use, the leaf sums of u * dh^3 and the
  * bad-cell count of the new state.  Waits for that step.  Any output

@@ -1,4 +1,7 @@
-"""Plain FP64 CPU oracle of the relaxing-TVD patch-group hydro path.
+"""Plain FP64 CPU oracle of the relaxing-TVD patch-group hydro path and of
+the pieces around it: individual time steps, the refinement-map rebuild,
+the red-black SOR Poisson solver and the gravity operator of the xyzGGzyx
+splitting.
 
 TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and
 the CPU-baseline leg of ``bench.py`` may import this package; the product

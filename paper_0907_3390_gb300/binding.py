@@ -29,6 +29,7 @@ EXPORTS = [
     "gamer_hydro_advance", "gamer_hydro_fixup", "gamer_hydro_advance_all",
     "gamer_hydro_check", "gamer_hydro_diagnose", "gamer_hydro_step", "gamer_hydro_step_pair",
     "gamer_hydro_set_time_steps", "gamer_hydro_flag", "gamer_hydro_refine_fill", "gamer_poisson_sor",
+    "gamer_gravity_update",
     "gamer_hydro_step_result",
     "gamer_hydro_diagnose_noalloc", "gamer_hydro_tune", "gamer_hydro_get_config",
     "gamer_hydro_set_profiling", "gamer_hydro_last_error",
@@ -90,6 +91,7 @@ def load(build_if_needed: bool = True) -> C.CDLL:
         L.gamer_hydro_refine_fill.argtypes = [H, hp, C.c_int, C.c_int, vp, vp, vp, C.c_int, vp]
         L.gamer_poisson_sor.argtypes = [C.c_int, C.c_int, vp, vp, C.c_double, C.c_double, C.c_int, C.c_double,
                                         vp, vp]
+        L.gamer_gravity_update.argtypes = [C.c_int, C.c_int, vp, vp, C.c_double, C.c_double, vp]
         L.gamer_hydro_step_result.argtypes = [H, dp, dp, dp, C.POINTER(C.c_int64)]
         L.gamer_hydro_diagnose_noalloc.argtypes = [C.c_double, C.c_int, hp, C.c_double, vp, dp, dp,
                                                    C.POINTER(C.c_int64)]
@@ -203,6 +205,16 @@ def gamer_poisson_sor(precision: int, rho, phi, coef: float, omega: float, max_i
     st = None if stream is None else getattr(stream, "cuda_stream", stream)
     _check(None, load().gamer_poisson_sor(precision, n, rho.data_ptr(), phi.data_ptr(), coef, omega, max_iter, tol,
                                           None if iters is None else iters.data_ptr(), st))
+
+
+def gamer_gravity_update(precision: int, u, phi, dh: float, dt: float, stream=None) -> None:
+    """u: one level's device state [5, 8 n, 8, 8, 8] (updated in place);
+    phi: device tensor [n, 18, 18, 18] of the same dtype."""
+    n = int(phi.shape[0])
+    if int(u.shape[1]) != 8 * n:
+        raise ValueError("u holds 8 patches per potential block")
+    st = None if stream is None else getattr(stream, "cuda_stream", stream)
+    _check(None, load().gamer_gravity_update(precision, n, u.data_ptr(), phi.data_ptr(), dh, dt, st))
 
 
 def gamer_hydro_step_pair(h, H, cfl: float) -> None:

@@ -12,6 +12,8 @@ Each translation unit is compiled in parallel, then linked with
 * regrid.cu: flag step and refinement fill of the refinement-map rebuild,
   ``-fmad=false`` (criteria in their plain order);
 * poisson.cu: red-black SOR Poisson solver of one patch group per block,
+  ``-fmad=false`` (FP64 in the oracle's order);
+* gravity.cu: the gravity operator of the xyzGGzyx splitting,
   ``-fmad=false`` (FP64 in the oracle's order).
 """
 from __future__ import annotations
@@ -39,6 +41,7 @@ UNITS = {
     "noalloc.cu": [],
     "regrid.cu": ["-fmad=false"],
     "poisson.cu": ["-fmad=false"],
+    "gravity.cu": ["-fmad=false"],
 }
 
 

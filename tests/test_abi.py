@@ -16,7 +16,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "gamer_hydro.h")).read()
-    return sorted(set(re.findall(r"\b(gamer_(?:hydro|poisson)_\w+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(gamer_(?:hydro|poisson|gravity)_\w+)\s*\(", src)))
 
 
 def test_header_matches_binding_exports():
@@ -51,6 +51,17 @@ def test_struct_layouts_match_header():
     # gamer_level_t: 2 int32 + double + 6 pointers; gamer_hierarchy_t: 2 int32 + ptr + u64
     assert C.sizeof(B.gamer_level_t) == 8 + 8 + 6 * 8
     assert C.sizeof(B.gamer_hierarchy_t) == 8 + 8 + 8
+
+
+def test_gravity_update_validates_before_any_cuda_call():
+    lib = B.load()
+    assert lib.gamer_gravity_update(7, 1, None, None, 0.1, 0.01, None) == B.GAMER_ERR_ARG
+    assert lib.gamer_gravity_update(B.GAMER_FP32, -1, None, None, 0.1, 0.01, None) == B.GAMER_ERR_ARG
+    assert lib.gamer_gravity_update(B.GAMER_FP32, 1, None, None, 0.0, 0.01, None) == B.GAMER_ERR_ARG
+    assert lib.gamer_gravity_update(B.GAMER_FP32, 1, None, None, 0.1, -1.0, None) == B.GAMER_ERR_ARG
+    assert lib.gamer_gravity_update(B.GAMER_FP64, 1, None, None, 0.1, float("nan"), None) == B.GAMER_ERR_ARG
+    assert lib.gamer_gravity_update(B.GAMER_FP32, 1, None, None, 0.1, 0.01, None) == B.GAMER_ERR_ARG
+    assert lib.gamer_gravity_update(B.GAMER_FP32, 0, None, None, 0.1, 0.01, None) == B.GAMER_OK
 
 
 def test_poisson_sor_validates_before_any_cuda_call():
