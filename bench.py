@@ -267,6 +267,7 @@ def _timing_event(torch):
 def run_ours(args, rank, world, dist):
     import torch
     from paper_0907_3390_gb300 import binding as B
+    from paper_0907_3390_gb300 import replicas as R
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
@@ -277,8 +278,7 @@ def run_ours(args, rank, world, dist):
     stream = torch.cuda.current_stream()
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        R.barrier(dist)
 
     S = B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP32, stream=stream)
     D = B.DeviceHierarchy(H, st, torch.float32, device=dev)
@@ -335,14 +335,7 @@ def run_ours(args, rank, world, dist):
         torch.cuda.synchronize()
         kern_ms.append(kev[0].elapsed_time(kev[1]))
     B.gamer_hydro_set_profiling(S.h, None, None)
-    t_local = step_ms / 1e3
-    if dist is not None:
-        t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
-    value = updates * args.steps * world / t_max
+    value, t_max = R.whole_job_rate(updates * args.steps, step_ms / 1e3, dist, dev)
     res = {"value": value, "ms_per_step": 1e3 * t_max / args.steps, "sets_per_step": sets,
            "updates_per_step": updates, "time_steps": "individual" if individual else "uniform"}
     # kernels per step: one level = the persistent sweep launch alone (it runs
@@ -386,14 +379,16 @@ def run_ours(args, rank, world, dist):
     res["conservation_drift_rel"] = float(np.max(np.abs(sums - s0) / (np.abs(s0) + 1e-30)))
     res["n_bad"] = n_bad
     extras = {}
-    if not args.quick and rank == 0:
-        extras = run_extras(args, B, torch, H, st, cells, dev, stream, updates)
+    if not args.quick:
+        # e2e on every rank at once (max over ranks); the rest on rank 0
+        extras["e2e"] = run_e2e(args, B, R, torch, H, st, dev, stream, updates, dist)
+        if rank == 0:
+            extras.update(run_extras(args, B, torch, H, st, cells, dev, stream, updates, world))
     S.close()
     return res, extras, cells, desc
 
 
-def run_extras(args, B, torch, H, st, cells, dev, stream, updates):
-    out = {}
+def run_e2e(args, B, R, torch, H, st, dev, stream, updates, dist):
     # ---- e2e through the C ABI with host buffers.  Every step takes its
     # input state from pinned host memory, advances it through the same
     # call as the timed step (whose last kernel writes the step result to
@@ -423,6 +418,7 @@ def run_extras(args, B, torch, H, st, cells, dev, stream, updates):
     for it in range(warm + n_e2e):
         if it == warm:
             torch.cuda.synchronize()
+            R.barrier(dist)
             e0.record(stream)
             s_in.wait_stream(stream)             # the first timed copy-in starts after e0
         b = it % NB
@@ -453,15 +449,20 @@ def run_extras(args, B, torch, H, st, cells, dev, stream, updates):
         stream.wait_event(ev_out[b])
     e1.record(stream)
     torch.cuda.synchronize()
+    R.barrier(dist)
     for S in solvers:
         B.gamer_hydro_step_result(S.h)
-    ms = e0.elapsed_time(e1) / n_e2e
+    rate, _ = R.whole_job_rate(updates * n_e2e, e0.elapsed_time(e1) / 1e3, dist, dev)
     nbytes = sum(x.numel() * 4 for x in host_in)
-    out["e2e"] = {"value": updates / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                  "d2h_bytes_per_step": nbytes + 88,      # + the step result (11 x 8 B)
-                  "pipeline": f"{NB} independent states in flight; copy-in, step and copy-out on 3 streams"}
     for S in solvers:
         S.close()
+    return {"value": rate, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes + 88,      # + the step result (11 x 8 B)
+            "pipeline": f"{NB} independent states in flight per GPU; copy-in, step and copy-out on 3 streams"}
+
+
+def run_extras(args, B, torch, H, st, cells, dev, stream, updates, world):
+    out = {}
 
     # ---- plain FP64 GPU path (one block per patch group, same whole-step
     # API) and the per-field L1 error of one FP32 sweep set against it (the
@@ -481,6 +482,7 @@ def run_extras(args, B, torch, H, st, cells, dev, stream, updates):
     B.gamer_hydro_step(S64.h, D64, CFL)
     D64.swap()
     torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(n64):
         B.gamer_hydro_step(S64.h, D64, CFL)
@@ -495,7 +497,10 @@ def run_extras(args, B, torch, H, st, cells, dev, stream, updates):
     S64.close()
     S32.close()
 
-    # ---- the oracle on the host cores, bounded sample
+    # ---- the oracle on the host cores, bounded sample (one process only:
+    # under torchrun the host cores are shared by the ranks)
+    if world > 1:
+        return out
     threads = os.cpu_count() or 1
     rate, sample, secs = cpu_oracle_rate(H, st, args.cpu_seconds, threads)
     rate1, sample1, secs1 = cpu_oracle_rate(H, st, max(1.0, args.cpu_seconds / 4), 1, max_groups=16)
@@ -796,7 +801,7 @@ def main():
             if k in extras:
                 line[k] = extras[k]
         if "fp64_plain" in extras:
-            line["fp32_over_fp64_plain"] = res["value"] / extras["fp64_plain"]["value"]
+            line["fp32_over_fp64_plain"] = res["value"] / world / extras["fp64_plain"]["value"]
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
