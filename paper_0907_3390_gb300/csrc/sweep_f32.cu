@@ -302,6 +302,94 @@ __device__ __noinline__ void prolong_cell(const LevelArgs<float>& L, const ItemT
                    (lp >> 2) & 1, x, y, z, val);
 }
 
+// Coarse-fine ghost cells x in [xa, xb) of the fine row (y, z) (group-local
+// fine coordinates, xb - xa <= 8: one half of the row's centre or one
+// edge) by Min-Mod interpolation, the same arithmetic as prolong_cell:
+// the row's coarse cells (x >> 1) are read once -- the coarse row with its
+// x-neighbours and the four side rows, every load of a variable issued
+// before the first is used -- and each coarse cell's limited slopes serve
+// both of its fine children.  dst: the shared-memory cell of x = xa,
+// variable 0.  Out of line like prolong_cell.
+__device__ __noinline__ void prolong_row(const LevelArgs<float>& L, const ItemTab& t, int y, int z, int xa, int xb,
+                                         float* dst) {
+    constexpr int MC = 4;                                  // coarse cells per call, at most
+    const int lp = t.par & 7;
+    const int px = lp & 1, py = (lp >> 1) & 1, pz = (lp >> 2) & 1;
+    const int cy = PS * py + (y >> 1), cz = PS * pz + (z >> 1);
+    const int ca = PS * px + (xa >> 1);
+    const int nc = PS * px + ((xb - 1) >> 1) - ca + 1;
+    const float sy = (y & 1) ? 1.0f : -1.0f, sz = (z & 1) ? 1.0f : -1.0f;
+    auto at = [&](int a, int b, int c) -> int {
+        const int s = resolve(t.csrc, t.cmask, a, b, c);
+        return (int)cell_offset(s < 0 ? 0 : s, a, b, c);   // s < 0 cannot pass host validation
+    };
+    // coarse row ca-1 .. ca+nc, side rows y-1, y+1, z-1, z+1 at ca .. ca+nc-1
+    int oc[MC + 2], oym[MC], oyp[MC], ozm[MC], ozp[MC];
+#pragma unroll
+    for (int i = 0; i < MC + 2; ++i)
+        if (i < nc + 2) oc[i] = at(ca - 1 + i, cy, cz);
+#pragma unroll
+    for (int i = 0; i < MC; ++i) {
+        if (i >= nc) continue;
+        oym[i] = at(ca + i, cy - 1, cz);
+        oyp[i] = at(ca + i, cy + 1, cz);
+        ozm[i] = at(ca + i, cy, cz - 1);
+        ozp[i] = at(ca + i, cy, cz + 1);
+    }
+    const size_t vs = (size_t)L.n_groups_c * 8 * 512;
+    const float w = (float)L.cw;
+#pragma unroll 1
+    for (int v = 0; v < NV; ++v) {
+        const float* p = L.uc + v * vs;
+        const float* pn = L.ucn != nullptr ? L.ucn + v * vs : nullptr;
+        float c[MC + 2], ym[MC], yp[MC], zm[MC], zp[MC];
+#pragma unroll
+        for (int i = 0; i < MC + 2; ++i)
+            if (i < nc + 2) c[i] = p[oc[i]];
+#pragma unroll
+        for (int i = 0; i < MC; ++i) {
+            if (i >= nc) continue;
+            ym[i] = p[oym[i]];
+            yp[i] = p[oyp[i]];
+            zm[i] = p[ozm[i]];
+            zp[i] = p[ozp[i]];
+        }
+        if (pn != nullptr) {
+            // individual time steps: the coarse state at the start of this
+            // level's step, linear in time between before and after the
+            // coarse sweep set
+#pragma unroll
+            for (int i = 0; i < MC + 2; ++i)
+                if (i < nc + 2) c[i] = c[i] + w * (pn[oc[i]] - c[i]);
+#pragma unroll
+            for (int i = 0; i < MC; ++i) {
+                if (i >= nc) continue;
+                ym[i] = ym[i] + w * (pn[oym[i]] - ym[i]);
+                yp[i] = yp[i] + w * (pn[oyp[i]] - yp[i]);
+                zm[i] = zm[i] + w * (pn[ozm[i]] - zm[i]);
+                zp[i] = zp[i] + w * (pn[ozp[i]] - zp[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < MC; ++i) {
+            if (i >= nc) continue;
+            const float U = c[i + 1];
+            const float Sx = minmod_slope(c[i], U, c[i + 2]);
+            const float Sy = minmod_slope(ym[i], U, yp[i]);
+            const float Sz = minmod_slope(zm[i], U, zp[i]);
+            const int x0 = 2 * (ca + i - PS * px);               // fine x of the child with sx = -1
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                const int x = x0 + dx;
+                if (x < xa || x >= xb) continue;
+                const float sx = dx ? 1.0f : -1.0f;
+                const float tt = (sx * Sx + sy * Sy) + sz * Sz;
+                dst[v * VS + (x - xa)] = U + 0.25f * tt;
+            }
+        }
+    }
+}
+
 // One padded x-row (yp, zp) of the block of item t.  SEG bit 0: the 16
 // centre cells (x in [0,16)); bit 1: the 3 + 3 edge cells; bit 2 / bit 3:
 // only the first / second half of the centre (one patch row each).  Every cell lies
@@ -309,7 +397,7 @@ __device__ __noinline__ void prolong_cell(const LevelArgs<float>& L, const ItemT
 // four 16-byte loads per variable and each edge one.  Outflow edges repeat
 // the centre's edge cell (zero gradient); cells of coarse regions are
 // interpolated one by one.
-template <int SEG>
+template <int SEG, bool ROWI = false>
 __device__ __forceinline__ void gather_row(float* sm, const SweepArgs<float>& a, const ItemTab& t,
                                            int yp, int zp) {
     const LevelArgs<float>& L = a.lv[t.level];
@@ -347,6 +435,9 @@ __device__ __forceinline__ void gather_row(float* sm, const SweepArgs<float>& a,
                     q[4 * j + 3] = c[v][j].w;
                 }
             }
+        } else if (ROWI) {
+            if (H0) prolong_row(L, t, y, z, 0, PS, d + NG);
+            if (H1) prolong_row(L, t, y, z, PS, GS, d + NG + PS);
         } else {
             for (int x = H0 ? 0 : PS; x < (H1 ? GS : PS); ++x) {
                 float val[NV];
@@ -392,6 +483,8 @@ __device__ __forceinline__ void gather_row(float* sm, const SweepArgs<float>& a,
                         d[v * VS + 21] = q.z;
                     }
                 }
+            } else if (ROWI) {
+                prolong_row(L, t, y, z, side ? GS : -NG, side ? GS + NG : 0, d + o);
             } else {
                 for (int k = 0; k < NG; ++k) {
                     float val[NV];
@@ -422,12 +515,12 @@ struct GatherSet {
 
 // Task r of set PH (set D is split into half rows so that every thread
 // gets one).
-template <int ORDER, int PH>
+template <int ORDER, int PH, bool ROWI = false>
 __device__ __forceinline__ void gather_task(float* sm, const SweepArgs<float>& a, const ItemTab& t, int r) {
     if (PH == 3) {
         const int row = r >> 1;
-        if (r & 1) gather_row<8>(sm, a, t, NG + row % GS, NG + row / GS);
-        else gather_row<4>(sm, a, t, NG + row % GS, NG + row / GS);
+        if (r & 1) gather_row<8, ROWI>(sm, a, t, NG + row % GS, NG + row / GS);
+        else gather_row<4, ROWI>(sm, a, t, NG + row % GS, NG + row / GS);
         return;
     }
     int yp, zp;
@@ -435,26 +528,26 @@ __device__ __forceinline__ void gather_task(float* sm, const SweepArgs<float>& a
         if (PH == 0) { yp = r % PD; zp = r / PD; }
         else if (PH == 1) { yp = ghost_row(r % 6); zp = r / 6; }
         else { yp = NG + r % GS; zp = ghost_row(r / GS); }
-        if (PH == 0) gather_row<2>(sm, a, t, yp, zp);
-        else gather_row<1>(sm, a, t, yp, zp);
+        if (PH == 0) gather_row<2, ROWI>(sm, a, t, yp, zp);
+        else gather_row<1, ROWI>(sm, a, t, yp, zp);
     } else {
         if (PH == 0) { yp = r % PD; zp = ghost_row(r / PD); }
         else if (PH == 1) { yp = ghost_row(r % 6); zp = NG + r / 6; }
         else { yp = NG + r % GS; zp = NG + r / GS; }
-        if (PH <= 1) gather_row<3>(sm, a, t, yp, zp);
-        else gather_row<2>(sm, a, t, yp, zp);
+        if (PH <= 1) gather_row<3, ROWI>(sm, a, t, yp, zp);
+        else gather_row<2, ROWI>(sm, a, t, yp, zp);
     }
 }
 
 // Tasks of set PH handed out through a shared-memory counter: threads that
 // finish their own phase work early (sweep columns, store rows) pick up the
 // remaining gather tasks.
-template <int ORDER, int PH>
+template <int ORDER, int PH, bool ROWI = false>
 __device__ __forceinline__ void gather_pool(float* sm, const SweepArgs<float>& a, const ItemTab& t, int* cnt) {
     for (;;) {
         const int r = atomicAdd(cnt, 1);
         if (r >= GatherSet<ORDER, PH>::N) break;
-        gather_task<ORDER, PH>(sm, a, t, r);
+        gather_task<ORDER, PH, ROWI>(sm, a, t, r);
     }
 }
 
@@ -638,7 +731,7 @@ __device__ __forceinline__ void finish_launch(const SweepArgs<float>& a, float* 
 // The first item of each CTA is gathered whole.
 constexpr int NT_F32 = 512;
 
-template <int ORDER, int LIM>
+template <int ORDER, int LIM, bool ROWI = false>
 __device__ __forceinline__ void sweep_first(float* sm, const SweepArgs<float>& a, const ItemTab& t,
                                             float lam, float* flux_g) {
     if (ORDER == 0) {
@@ -646,7 +739,7 @@ __device__ __forceinline__ void sweep_first(float* sm, const SweepArgs<float>& a
         const int c = threadIdx.x;
         if (c >= PD * PD) return;
         const int yp = c % PD, zp = c / PD;
-        if (yp >= NG && yp < NG + GS) gather_row<1>(sm, a, t, yp, zp);
+        if (yp >= NG && yp < NG + GS) gather_row<1, ROWI>(sm, a, t, yp, zp);
         float* p = sm + yp * XP + zp * (PD * XP);
         float* fl = nullptr;
         if (flux_g != nullptr && yp >= NG && yp < NG + GS && zp >= NG && zp < NG + GS)
@@ -657,7 +750,11 @@ __device__ __forceinline__ void sweep_first(float* sm, const SweepArgs<float>& a
     }
 }
 
-template <int ORDER, int LIM>
+// ROWI: coarse-fine ghost rows interpolated a row segment per call
+// (prolong_row), for launches that include a level with a coarser level;
+// launches over level 0 alone have no coarse regions and keep the per-cell
+// fallback, whose code is smaller.
+template <int ORDER, int LIM, bool ROWI>
 __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> args) {
     extern __shared__ float sm[];
     ItemTab* tab = reinterpret_cast<ItemTab*>(sm + NV * VS);     // [2]
@@ -682,8 +779,8 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> 
         // centres of the rows with yp in [3,19))
         for (int r = tid; r < PD * PD; r += NT_F32) {
             const int yp = r % PD, zp = r / PD;
-            if (ORDER == 0 && yp >= NG && yp < NG + GS) gather_row<2>(sm, args, tab[0], yp, zp);
-            else gather_row<3>(sm, args, tab[0], yp, zp);
+            if (ORDER == 0 && yp >= NG && yp < NG + GS) gather_row<2, ROWI>(sm, args, tab[0], yp, zp);
+            else gather_row<3, ROWI>(sm, args, tab[0], yp, zp);
         }
 
         for (;;) {
@@ -698,7 +795,7 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> 
             const int cur_item = cur.item;
             const int cur_g = cur.g;
 
-            sweep_first<ORDER, LIM>(sm, args, cur, lam, fg);
+            sweep_first<ORDER, LIM, ROWI>(sm, args, cur, lam, fg);
             __syncthreads();
             if (tid < 11 * 32) {
                 sweep<ORDER, 1, LIM>(sm, lam, args.gamma, args.gm1, fg, 11 * 32);
@@ -706,7 +803,7 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> 
                 build_tab(nxt, args, next, 11 * 32);
                 if (tid == 11 * 32) prefetch_item(args, next);
                 asm volatile("bar.sync 1, 160;" ::: "memory");      // warps 11..15: tables ready
-                gather_pool<ORDER, 0>(sm, args, nxt, &s_cnt[0]);
+                gather_pool<ORDER, 0, ROWI>(sm, args, nxt, &s_cnt[0]);
             }
             __syncthreads();
             if (tid < 8 * 32) {
@@ -716,7 +813,7 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> 
                     s_item[1] = has_next ? atomicAdd(args.queue, 1) : next;
                 }
             } else if (has_next) {
-                gather_pool<ORDER, 1>(sm, args, nxt, &s_cnt[1]);
+                gather_pool<ORDER, 1, ROWI>(sm, args, nxt, &s_cnt[1]);
             }
             __syncthreads();
             if (tid == 0) s_cnt[0] = s_cnt[1] = 0;
@@ -726,8 +823,8 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> 
             if (ORDER == 1) {
                 // sets C (x-edges of the interior rows) and D (their centres, by halves)
                 for (int r = tid; r < GS * GS + 2 * GS * GS; r += NT_F32) {
-                    if (r < GS * GS) gather_row<2>(sm, args, tab[slot], NG + r % GS, NG + r / GS);
-                    else gather_task<ORDER, 3>(sm, args, tab[slot], r - GS * GS);
+                    if (r < GS * GS) gather_row<2, ROWI>(sm, args, tab[slot], NG + r % GS, NG + r / GS);
+                    else gather_task<ORDER, 3, ROWI>(sm, args, tab[slot], r - GS * GS);
                 }
             }
         }
@@ -968,8 +1065,9 @@ static cudaError_t set_attr(K k) {
 cudaError_t sweep_f32_init() {
     cudaError_t e = cudaSuccess;
     const cudaError_t r[] = {
-        set_attr(k_sweep_f32<0, 0>), set_attr(k_sweep_f32<0, 1>), set_attr(k_sweep_f32<1, 0>),
-        set_attr(k_sweep_f32<1, 1>), set_attr(k_sweep_f32_simple<0, 0, 256>),
+        set_attr(k_sweep_f32<0, 0, false>), set_attr(k_sweep_f32<0, 1, false>), set_attr(k_sweep_f32<1, 0, false>),
+        set_attr(k_sweep_f32<1, 1, false>), set_attr(k_sweep_f32<0, 0, true>), set_attr(k_sweep_f32<0, 1, true>),
+        set_attr(k_sweep_f32<1, 0, true>), set_attr(k_sweep_f32<1, 1, true>), set_attr(k_sweep_f32_simple<0, 0, 256>),
         set_attr(k_sweep_f32_simple<0, 1, 256>), set_attr(k_sweep_f32_simple<1, 0, 256>),
         set_attr(k_sweep_f32_simple<1, 1, 256>), set_attr(k_sweep_f32_simple<0, 0, 512>),
         set_attr(k_sweep_f32_simple<0, 1, 512>), set_attr(k_sweep_f32_simple<1, 0, 512>),
@@ -981,7 +1079,10 @@ cudaError_t sweep_f32_init() {
 
 template <int ORDER, int LIM>
 static cudaError_t launch_pipe(const SweepArgs<float>& a, int grid, cudaStream_t st) {
-    k_sweep_f32<ORDER, LIM><<<grid, NT_F32, SMEM_F32, st>>>(a);
+    bool coarse = false;                 // some level of the launch has a coarser level
+    for (int l = 0; l < a.n_levels; ++l) coarse = coarse || a.lv[l].uc != nullptr;
+    if (coarse) k_sweep_f32<ORDER, LIM, true><<<grid, NT_F32, SMEM_F32, st>>>(a);
+    else k_sweep_f32<ORDER, LIM, false><<<grid, NT_F32, SMEM_F32, st>>>(a);
     return cudaGetLastError();
 }
 
