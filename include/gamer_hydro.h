@@ -182,7 +182,8 @@ int gamer_hydro_step(gamer_hydro_t h, const gamer_hierarchy_t *H, double cfl);
  * published, so the two sets overlap and share one start-up and one tail;
  * waits are bounded (about a second), and a wait that gave up makes
  * gamer_hydro_step_result return GAMER_ERR_TIMEOUT.  Other hierarchies run
- * the two sets as two steps.  Captured as a CUDA graph like
+ * the two sets as two steps, the diagnostics only after the second (the
+ * xyz set keeps dt either way).  Captured as a CUDA graph like
  * gamer_hydro_step.  Asynchronous; results via gamer_hydro_step_result. */
 int gamer_hydro_step_pair(gamer_hydro_t h, const gamer_hierarchy_t *H, double cfl);
 

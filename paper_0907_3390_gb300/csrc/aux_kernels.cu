@@ -1,5 +1,7 @@
 // aux_kernels.cu -- coarse-fine fix-up and diagnostics (CFL maxima,
 // conservation sums, positivity count), for both element types.
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -162,9 +164,13 @@ __global__ void __launch_bounds__(NT_DIAG) k_diag(const DiagArgs<T> a) {
     const int g = item - L.item0;
     const size_t vstride = (size_t)L.n_groups * 8 * 512;
     const T* base = L.u + ((size_t)g << 12);
-    unsigned long long smax = 0ull;
+    // the speed maximum as the bit pattern of a non-negative T (a NaN wins),
+    // widened to double once per thread
+    using Bits = typename std::conditional<sizeof(T) == 4, unsigned, unsigned long long>::type;
+    Bits smax_t = 0;
     Acc acc[NV];
     int bad = 0;
+#pragma unroll 4
     for (int i = threadIdx.x; i < CELLS_PG; i += NT_DIAG) {
         const int patch = i >> 9;
         const bool leaf = L.child == nullptr || L.child[8 * g + patch] < 0;
@@ -177,14 +183,18 @@ __global__ void __launch_bounds__(NT_DIAG) k_diag(const DiagArgs<T> a) {
         }
         T s, P;
         speed_pressure(u, a.gamma, a.gm1, s, P);
-        const unsigned long long sb = (unsigned long long)__double_as_longlong((double)s);
-        smax = sb > smax ? sb : smax;
+        Bits sb;
+        memcpy(&sb, &s, sizeof(T));
+        smax_t = sb > smax_t ? sb : smax_t;
         if (leaf) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) acc[v].add(u[v]);
             if (!finite || !(u[0] > T(0)) || !(P > T(0))) ++bad;
         }
     }
+    T smax_v;
+    memcpy(&smax_v, &smax_t, sizeof(T));
+    const unsigned long long smax = (unsigned long long)__double_as_longlong((double)smax_v);
     __shared__ double s_sum[NV][NT_DIAG];
     __shared__ unsigned long long s_max[NT_DIAG];
     __shared__ int s_bad[NT_DIAG];

@@ -780,7 +780,9 @@ int enqueue_pair(gamer_hydro_t h, const gamer_hierarchy_t* H, cudaStream_t st, d
     if (h->individual && H->n_levels > 1) return enqueue_cycle(h, H, st, cfl);
     const int n = H->levels[0].n_groups;
     if (!(h->precision == GAMER_FP32 && H->n_levels == 1 && n > 0 && h->pair_n == n)) {
-        int r = enqueue_step(h, H, st, true, cfl);
+        // the xyz set keeps dt and its state is not the pair's result: no
+        // diagnostics after it, as in the fused pair launch
+        int r = enqueue_step(h, H, st, false, cfl);
         if (r) return r;
         for (int l = 0; l < H->n_levels; ++l) h->parity[l] ^= 1;
         SwappedHierarchy S(H);
