@@ -48,7 +48,7 @@ enum {
     GAMER_ERR_CUDA = -2,         /* a CUDA call failed                        */
     GAMER_ERR_MAP = -3,          /* inconsistent neighbour / parent / child map */
     GAMER_ERR_TIMEOUT = -4,      /* a bounded device-side wait gave up        */
-    GAMER_ERR_UNSUPPORTED = -5,  /* valid request this build does not offer   */
+    GAMER_ERR_UNSUPPORTED = -5,  /* valid request the library does not offer */
     GAMER_ERR_STATE = -6         /* call out of order for the handle          */
 };
 
@@ -331,7 +331,7 @@ int gamer_hydro_diagnose_noalloc(double gamma, int precision, const gamer_hierar
                                  double cfl, void *cuda_stream, double *dt_out, double sums[5],
                                  int64_t *n_bad);
 
-/* Autotuner: times the launch configurations this build offers on the
+/* Autotuner: times the launch configurations the library offers on the
  * caller's hierarchy and keeps the fastest for the handle.  FP32 handles
  * choose between the pipelined persistent kernel (512 threads: the next
  * work item's ghost slabs gathered by warps idle in sweeps 2 and 3) and the
