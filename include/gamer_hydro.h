@@ -187,6 +187,18 @@ int gamer_hydro_step(gamer_hydro_t h, const gamer_hierarchy_t *H, double cfl);
  * gamer_hydro_step.  Asynchronous; results via gamer_hydro_step_result. */
 int gamer_hydro_step_pair(gamer_hydro_t h, const gamer_hierarchy_t *H, double cfl);
 
+/* Test hook for the failure path of the fused pair launch: the next
+ * gamer_hydro_step_pair on a single-level FP32 hierarchy does not publish
+ * the xyz result of patch group `group` (level 0), a mark that nothing else
+ * sets.  The zyx items that read it wait until their bound runs out (about
+ * a second), later waits give up at once, the launch finishes, and
+ * gamer_hydro_step_result returns GAMER_ERR_TIMEOUT; the state that step
+ * leaves is not valid, the handle and the CUDA context stay usable.  The
+ * hook applies to one call (that call is launched directly, not through a
+ * graph); -1 clears it, a group outside the level publishes everything.
+ * GAMER_ERR_ARG for group < -1. */
+int gamer_hydro_test_withhold(gamer_hydro_t h, int group);
+
 /* Time stepping of multi-level hierarchies (Sec. 2.1).
  * GAMER_TIME_STEPS_UNIFORM (default): one dt for every level, as the paper
  * does with self-gravity.  GAMER_TIME_STEPS_INDIVIDUAL: every level takes

@@ -73,6 +73,7 @@ struct PairArgs {
     unsigned* epoch;    // launch counter; the last CTA advances it
     unsigned* status;   // nonzero after a wait gave up (reported, then cleared)
     const int* order1;  // [n] zyx work order
+    int hold;           // a group whose xyz mark is not published (the failure-path test), or -1
 };
 
 template <typename T>

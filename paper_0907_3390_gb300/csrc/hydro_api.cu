@@ -63,6 +63,7 @@ struct gamer_hydro_s {
     unsigned* d_ready = nullptr;  // [pair_n] publication marks of pair launches
     int* d_order1 = nullptr;      // [pair_n] zyx work order of pair launches
     int pair_n = 0;
+    int hold = -1;                // group whose mark the next pair launch withholds (test hook)
     unsigned long long* d_pg_max = nullptr;
     double* d_pg_sum = nullptr;
     int* d_pg_bad = nullptr;
@@ -808,7 +809,7 @@ int enqueue_pair(gamer_hydro_t h, const gamer_hierarchy_t* H, cudaStream_t st, d
     // after a zyx set the next set is an xyz set: take the new dt
     a.step = StepSink{h->d_step, h->h_step_dev, h->d_dt, cfl, H->levels[0].dh, 1, n};
     a.pair = PairArgs{h->d_ready, reinterpret_cast<unsigned*>(h->d_queue + 2),
-                      reinterpret_cast<unsigned*>(h->d_queue + 3), h->d_order1};
+                      reinterpret_cast<unsigned*>(h->d_queue + 3), h->d_order1, h->hold};
     cudaError_t e = cudaSuccess;
     if (h->prof_ev[0]) e = cudaEventRecord(h->prof_ev[0], st);
     if (e == cudaSuccess) e = launch_sweep_pair(a, h->limiter, std::max(1, std::min(2 * n, h->sm_count)), st);
@@ -922,6 +923,13 @@ int gamer_hydro_set_parity(gamer_hydro_t h, int level, int parity) {
     if (level < 0 || level >= 32 || (parity != 0 && parity != 1))
         return fail(h, GAMER_ERR_ARG, "level must be in [0,32) and parity 0 or 1");
     h->parity[level] = parity;
+    return GAMER_OK;
+}
+
+int gamer_hydro_test_withhold(gamer_hydro_t h, int group) {
+    if (!h) return GAMER_ERR_ARG;
+    if (group < -1) return fail(h, GAMER_ERR_ARG, "group must be -1 or a patch group of level 0");
+    h->hold = group;
     return GAMER_OK;
 }
 
@@ -1164,8 +1172,12 @@ int gamer_hydro_step_pair(gamer_hydro_t h, const gamer_hierarchy_t* H, double cf
         h->dt_ready = true;
         h->dt_version = h->version;
     }
-    if (h->prof_ev[0]) {
-        if ((r = enqueue_pair(h, H, h->stream, cfl))) return r;
+    if (h->prof_ev[0] || h->hold >= 0) {
+        // launched directly: profiling events cannot be timed inside graphs,
+        // and a withheld mark is a one-off that no graph should keep
+        r = enqueue_pair(h, H, h->stream, cfl);
+        h->hold = -1;
+        if (r) return r;
         CK(h, cudaEventRecord(h->step_event, h->stream));
         return GAMER_OK;
     }
@@ -1208,8 +1220,10 @@ int gamer_hydro_step_result(gamer_hydro_t h, double* dt_used, double* dt_next, d
     CK(h, cudaEventSynchronize(h->step_event));
     const StepOut& o = *h->h_step;
     if (o.steps == 0) return fail(h, GAMER_ERR_STATE, "no step has completed on this handle");
-    if (o.status != 0)
+    if (o.status != 0) {
+        h->dt_ready = false;          // the dt that launch left is not trusted: the next step takes Eq. CFL anew
         return fail(h, GAMER_ERR_TIMEOUT, "a dependency wait of the last pair launch gave up; its result is invalid");
+    }
     if (dt_used) *dt_used = o.dt_used;
     if (dt_next) *dt_next = o.dt_next;
     if (sums)

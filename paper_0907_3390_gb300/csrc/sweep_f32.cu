@@ -877,7 +877,7 @@ __device__ __forceinline__ void wait_inputs(const SweepArgs<float>& a, int g, un
 // fence orders them (cumulatively) before the mark.
 __device__ __forceinline__ void publish(const SweepArgs<float>& a, int g, unsigned target) {
     __threadfence();
-    st_release_u32(a.pair.ready + g, target);
+    if (g != a.pair.hold) st_release_u32(a.pair.ready + g, target);
 }
 
 // Pair launch: the xyz set and then the zyx set of one level with the same

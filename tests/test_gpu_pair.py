@@ -121,3 +121,39 @@ def test_pair_needs_xyz_parity():
     B.gamer_hydro_step_pair(S.h, D, 0.5)
     assert B.gamer_hydro_step_result(S.h)[3] == 0
     S.close()
+
+
+def test_withheld_mark_times_out_and_the_handle_recovers():
+    """The failure path of the pair launch without a fault: one group's xyz
+    mark is withheld (a flag that nothing sets), the zyx items that read it
+    wait until their bound runs out, the launch finishes and the step
+    reports GAMER_ERR_TIMEOUT; the next pair on the same handle and context
+    is correct again (equal to a fresh handle's pair, bit for bit)."""
+    import time
+    H, st = CASES["2x2x2"]()
+    S = B.Solver(G, 0, B.GAMER_FP32)
+    D = B.DeviceHierarchy(H, st, torch.float32)
+    B.gamer_hydro_step_pair(S.h, D, 0.5)
+    assert B.gamer_hydro_step_result(S.h)[3] == 0
+    B.gamer_hydro_test_withhold(S.h, 3)
+    t0 = time.perf_counter()
+    B.gamer_hydro_step_pair(S.h, D, 0.5)
+    with pytest.raises(B.GamerError) as e:
+        B.gamer_hydro_step_result(S.h)
+    waited = time.perf_counter() - t0
+    assert e.value.code == B.GAMER_ERR_TIMEOUT
+    assert waited < 30.0, waited
+    # the same handle, a fresh state: one pair, against a fresh handle
+    D2 = B.DeviceHierarchy(H, st, torch.float32)
+    B.gamer_hydro_step_pair(S.h, D2, 0.5)
+    assert B.gamer_hydro_step_result(S.h)[3] == 0
+    R = B.Solver(G, 0, B.GAMER_FP32)
+    D3 = B.DeviceHierarchy(H, st, torch.float32)
+    B.gamer_hydro_step_pair(R.h, D3, 0.5)
+    B.gamer_hydro_step_result(R.h)
+    assert torch.equal(D2.u[0], D3.u[0])
+    with pytest.raises(B.GamerError) as e:
+        B.gamer_hydro_test_withhold(S.h, -2)
+    assert e.value.code == B.GAMER_ERR_ARG
+    S.close()
+    R.close()
