@@ -82,6 +82,7 @@ def lib():
             L.orc_refine_fill.argtypes = [C.POINTER(_Level), C.c_int, C.c_int, C.POINTER(C.c_int32),
                                           C.POINTER(C.c_int32), dp, C.c_int, dp]
             L.orc_gravity_level.argtypes = [dp, C.c_int, dp, C.c_double, C.c_double]
+            L.orc_poisson_prepare.argtypes = [C.POINTER(_Level), C.c_int, C.c_int, dp, dp, dp]
             L.orc_sor_group.restype = C.c_int
             L.orc_sor_group.argtypes = [dp, dp, C.c_double, C.c_double, C.c_int, C.c_double, dp]
             L.orc_cfl_dt_steps.restype = C.c_double
@@ -247,6 +248,20 @@ class OracleLevels:
         if r != 0:
             raise ValueError(f"orc_gather_block: {r}")
         return out
+
+    def poisson_prepare(self, l: int, phi_c: np.ndarray):
+        """SOR inputs of level l >= 1 (orc_poisson_prepare): (phi blocks
+        [n][18][18][18] interpolated from the coarser level's potential phi_c
+        [8 n_c][8][8][8], density blocks [n][16][16][16])."""
+        self._refresh()
+        n = self.H.levels[l].n_groups
+        pc = np.ascontiguousarray(phi_c, dtype=np.float64)
+        phi = np.empty((n, 18, 18, 18))
+        rho = np.empty((n, 16, 16, 16))
+        r = lib().orc_poisson_prepare(self._arr, self.n, l, _dp(pc), _dp(phi), _dp(rho))
+        if r != 0:
+            raise ValueError(f"orc_poisson_prepare: {r}")
+        return phi, rho
 
     def gravity(self, l: int, phi: np.ndarray, dt: float) -> None:
         """The gravity operator G over dt on level l's state, in place

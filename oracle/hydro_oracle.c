@@ -815,6 +815,53 @@ int orc_sor_group(double *phi, const double *rho, double coef, double omega, int
     return it;
 }
 
+/* Inputs of the SOR solver of level l >= 1 (Sec. 2.3; reading R26): for
+ * every patch group g of level l, phi_blk[g] ([18][18][18], x fastest) is
+ * the Min-Mod interpolation (reading R8) of the coarser level's potential
+ * phi_c ([8 n_c][8][8][8], the level layout) at every cell of the group and
+ * of its one-cell ghost layer -- the ghost layer is the Dirichlet boundary of
+ * the group's problem, which the paper fills from the level one coarser,
+ * the interior the initial guess -- and rho_blk[g] ([16][16][16], x fastest)
+ * is the group's density from the level's state. */
+int orc_poisson_prepare(const orc_level *lv, int n_levels, int l, const double *phi_c, double *phi_blk,
+                        double *rho_blk)
+{
+    if (l < 1 || l >= n_levels || n_levels > MAXLV)
+        return ORC_ERR_ARG;
+    const int P = GS + 2;
+    orc_level tmp[MAXLV];
+    memcpy(tmp, lv, (size_t)n_levels * sizeof(orc_level));
+    /* the coarser level with the potential as its variable 0 (the other
+     * variables are interpolated alongside and dropped) */
+    const size_t ncell_c = (size_t)lv[l - 1].n_groups * 8 * PS * PS * PS;
+    double *uc = (double *)calloc(NV * ncell_c, sizeof(double));
+    if (uc == NULL)
+        return ORC_ERR_ARG;
+    memcpy(uc, phi_c, ncell_c * sizeof(double));
+    tmp[l - 1].u = uc;
+    tmp[l - 1].u_new = NULL;
+    tmp[l].coarse_w = 0.0;
+    int err = 0;
+    for (int g = 0; g < lv[l].n_groups && !err; g++) {
+        for (int z = -1; z <= GS && !err; z++)
+            for (int y = -1; y <= GS && !err; y++)
+                for (int x = -1; x <= GS; x++) {
+                    double val[NV];
+                    if (prolong_fetch(tmp, l, g, x, y, z, val) != 0) {
+                        err = 1;
+                        break;
+                    }
+                    phi_blk[(size_t)g * P * P * P + ((z + 1) * P + (y + 1)) * P + (x + 1)] = val[0];
+                }
+        for (int z = 0; z < GS; z++)
+            for (int y = 0; y < GS; y++)
+                for (int x = 0; x < GS; x++)
+                    rho_blk[(size_t)g * GS * GS * GS + (z * GS + y) * GS + x] = lv[l].u[cell_index(&lv[l], g, 0, x, y, z)];
+    }
+    free(uc);
+    return err ? ORC_ERR_MAP : ORC_OK;
+}
+
 /* ------------------------------------------------------- gravity (G) */
 
 /* The gravity operator G of the split scheme (Sec. 2.3: Eqs. MomConserve

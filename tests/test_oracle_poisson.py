@@ -120,3 +120,62 @@ def test_stopping_rule():
     _, ita, ra = oracle.sor_group(phi, rho, 1.0, 1.5, 1000, 1e-6)
     _, itb, rb = oracle.sor_group(phi, rho, 1.0, 1.5, 1000, 1e-10)
     assert 1 < ita < itb < 1000 and rb < ra
+
+
+# ------------------------------------------ SOR inputs of a refined level
+
+def _two_level_central():
+    from paper_0907_3390_gb300 import hierarchy as hm
+
+    def score(level, centres):
+        x, y, z = (centres[a][:, 0, 0, 0] for a in range(3))
+        return 0.2 - np.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2)
+    return hm.build_hierarchy((4, 4, 4), score, 2)
+
+
+def _states(H):
+    from paper_0907_3390_gb300 import workloads as wl
+    return wl.level_fields(H, lambda x, y, z, dh: (1.0 + 0.5 * np.sin(7 * x) * np.cos(5 * y) + 0.2 * z,
+                                                  0 * x, 0 * x, 0 * x, 1.0 + 0 * x))
+
+
+def test_prepare_linear_potential_exact():
+    """Min-Mod interpolation (R8) is exact on linear data, so a linear coarse
+    potential gives the same linear function at every fine cell and ghost
+    cell of every group (reading R26; the refined region lies far from the
+    periodic boundary, so no stencil wraps)."""
+    H = _two_level_central()
+    st = _states(H)
+    a = (0.3, 1.7, -0.6, 0.9)
+    c0 = H.cell_centres(0)
+    phi_c = a[0] + a[1] * c0[0] + a[2] * c0[1] + a[3] * c0[2]
+    O = oracle.OracleLevels(H, st)
+    phi, _ = O.poisson_prepare(1, phi_c)
+    L1 = H.levels[1]
+    i = np.arange(P) - 1 + 0.5
+    for g in range(L1.n_groups):
+        gx, gy, gz = (16 * L1.coords[g] + 0.0)
+        z, y, x = np.meshgrid((gz + i) * L1.dh, (gy + i) * L1.dh, (gx + i) * L1.dh, indexing="ij")
+        want = a[0] + a[1] * x + a[2] * y + a[3] * z
+        assert np.allclose(phi[g], want, rtol=0, atol=1e-12), g
+
+
+def test_prepare_density_blocks():
+    """The density blocks are the level's density, rearranged from the patch
+    layout to one x-fastest 16^3 block per group."""
+    H = _two_level_central()
+    st = _states(H)
+    c0 = H.cell_centres(0)
+    O = oracle.OracleLevels(H, st)
+    _, rho = O.poisson_prepare(1, np.zeros_like(c0[0]))
+    n = H.levels[1].n_groups
+    u0 = np.asarray(st[1][0]).reshape(n, 2, 2, 2, 8, 8, 8)          # g, pz, py, px, z, y, x
+    want = u0.transpose(0, 1, 4, 2, 5, 3, 6).reshape(n, 16, 16, 16)
+    assert np.array_equal(rho, want)
+
+
+def test_prepare_rejects_level_zero():
+    H = _two_level_central()
+    O = oracle.OracleLevels(H, _states(H))
+    with pytest.raises(ValueError):
+        O.poisson_prepare(0, np.zeros(1))
