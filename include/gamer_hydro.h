@@ -297,6 +297,22 @@ int gamer_poisson_sor(int precision, int n_groups, const void *rho, void *phi, d
 int gamer_gravity_update(int precision, int n_groups, void *u, const void *phi, double dh, double dt,
                          void *cuda_stream);
 
+/* Inputs of the SOR problems of refined level `level` >= 1 of H (Sec. 2.3):
+ * for every patch group of that level, phi_blocks [n][18][18][18] (x
+ * fastest; the layout gamer_poisson_sor and gamer_gravity_update take) gets
+ * at every cell -- the one-cell ghost layer, which is the Dirichlet
+ * boundary, and the 16^3 interior, the initial guess -- the Min-Mod
+ * interpolation (as for the coarse-fine ghosts of the hydro step) of
+ * phi_c, the potential of level-1 in the level layout [8 n_c][8][8][8];
+ * rho_blocks [n][16][16][16] (x fastest) gets the group's density from the
+ * level's state u.  All pointers are device memory of the handle's
+ * precision.  The maps are validated as for the step (GAMER_ERR_MAP);
+ * GAMER_ERR_ARG for level 0 or missing pointers.  Asynchronous, on the
+ * handle's stream.  The root level's potential (an FFT solve in the paper)
+ * is the caller's. */
+int gamer_poisson_prepare(gamer_hydro_t h, const gamer_hierarchy_t *H, int level, const void *phi_c,
+                          void *phi_blocks, void *rho_blocks);
+
 /* Result of the last gamer_hydro_step or gamer_hydro_step_pair: the dt it
  * used, the dt the next step will use, the leaf sums of u * dh^3 and the
  * bad-cell count of the new state.  Waits for that step.  Any output

@@ -29,7 +29,7 @@ EXPORTS = [
     "gamer_hydro_advance", "gamer_hydro_fixup", "gamer_hydro_advance_all",
     "gamer_hydro_check", "gamer_hydro_diagnose", "gamer_hydro_step", "gamer_hydro_step_pair",
     "gamer_hydro_set_time_steps", "gamer_hydro_flag", "gamer_hydro_refine_fill", "gamer_poisson_sor",
-    "gamer_gravity_update", "gamer_hydro_test_withhold",
+    "gamer_gravity_update", "gamer_hydro_test_withhold", "gamer_poisson_prepare",
     "gamer_hydro_step_result",
     "gamer_hydro_diagnose_noalloc", "gamer_hydro_tune", "gamer_hydro_get_config",
     "gamer_hydro_set_profiling", "gamer_hydro_last_error",
@@ -93,6 +93,7 @@ def load(build_if_needed: bool = True) -> C.CDLL:
                                         vp, vp]
         L.gamer_gravity_update.argtypes = [C.c_int, C.c_int, vp, vp, C.c_double, C.c_double, vp]
         L.gamer_hydro_test_withhold.argtypes = [H, C.c_int]
+        L.gamer_poisson_prepare.argtypes = [H, hp, C.c_int, vp, vp, vp]
         L.gamer_hydro_step_result.argtypes = [H, dp, dp, dp, C.POINTER(C.c_int64)]
         L.gamer_hydro_diagnose_noalloc.argtypes = [C.c_double, C.c_int, hp, C.c_double, vp, dp, dp,
                                                    C.POINTER(C.c_int64)]
@@ -206,6 +207,13 @@ def gamer_poisson_sor(precision: int, rho, phi, coef: float, omega: float, max_i
     st = None if stream is None else getattr(stream, "cuda_stream", stream)
     _check(None, load().gamer_poisson_sor(precision, n, rho.data_ptr(), phi.data_ptr(), coef, omega, max_iter, tol,
                                           None if iters is None else iters.data_ptr(), st))
+
+
+def gamer_poisson_prepare(h, H, level: int, phi_c, phi_blocks, rho_blocks) -> None:
+    """phi_c: device tensor [8 n_c, 8, 8, 8] (level-1 potential); phi_blocks
+    [n, 18, 18, 18] and rho_blocks [n, 16, 16, 16] are filled."""
+    _check(h, load().gamer_poisson_prepare(h, H.struct(), level, phi_c.data_ptr(), phi_blocks.data_ptr(),
+                                           rho_blocks.data_ptr()))
 
 
 def gamer_hydro_test_withhold(h, group: int) -> None:

@@ -926,6 +926,34 @@ int gamer_hydro_set_parity(gamer_hydro_t h, int level, int parity) {
     return GAMER_OK;
 }
 
+int gamer_poisson_prepare(gamer_hydro_t h, const gamer_hierarchy_t* H, int level, const void* phi_c,
+                          void* phi_blocks, void* rho_blocks) {
+    if (!h) return GAMER_ERR_ARG;
+    if (!phi_c || !phi_blocks || !rho_blocks)
+        return fail(h, GAMER_ERR_ARG, "phi_c, phi_blocks and rho_blocks are required");
+    CK(h, cudaSetDevice(h->device));
+    int r = prepare(h, H);
+    if (r) return r;
+    if ((r = check_level_arg(h, H, level))) return r;
+    if (level < 1) return fail(h, GAMER_ERR_ARG, "level 0 has no coarser level to take the boundary from");
+    const gamer_level_t& L = H->levels[level];
+    const gamer_level_t& C = H->levels[level - 1];
+    if (L.n_groups == 0) return GAMER_OK;
+    if (!L.u) return fail(h, GAMER_ERR_ARG, "u is NULL");
+    if (h->precision == GAMER_FP32) {
+        PrepArgs<float> a{static_cast<const float*>(phi_c), C.nbr, C.n_groups, L.parent,
+                          static_cast<const float*>(L.u), L.n_groups, static_cast<float*>(phi_blocks),
+                          static_cast<float*>(rho_blocks)};
+        CK(h, launch_poisson_prepare<float>(a, h->stream));
+    } else {
+        PrepArgs<double> a{static_cast<const double*>(phi_c), C.nbr, C.n_groups, L.parent,
+                           static_cast<const double*>(L.u), L.n_groups, static_cast<double*>(phi_blocks),
+                           static_cast<double*>(rho_blocks)};
+        CK(h, launch_poisson_prepare<double>(a, h->stream));
+    }
+    return GAMER_OK;
+}
+
 int gamer_hydro_test_withhold(gamer_hydro_t h, int group) {
     if (!h) return GAMER_ERR_ARG;
     if (group < -1) return fail(h, GAMER_ERR_ARG, "group must be -1 or a patch group of level 0");

@@ -60,6 +60,20 @@ template <typename T>
 cudaError_t launch_flag(const FlagArgs<T>& a, cudaStream_t st);
 
 template <typename T>
+struct PrepArgs {
+    const T* phi_c;       // coarser level's potential [8 n_c][8][8][8]
+    const int* nbrc;      // coarser level's map
+    int n_c;              // coarser level's groups
+    const int* parent;    // [n] parent patch (on the coarser level) of every group
+    const T* u;           // the level's state (density = variable 0)
+    int n;                // the level's groups
+    T* phi_blk;           // [n][18][18][18] output
+    T* rho_blk;           // [n][16][16][16] output
+};
+template <typename T>
+cudaError_t launch_poisson_prepare(const PrepArgs<T>& a, cudaStream_t st);
+
+template <typename T>
 struct RefineArgs {
     const T* uc;          // parent level's state
     const int* nbrc;      // parent level's map

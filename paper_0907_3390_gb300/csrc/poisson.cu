@@ -130,6 +130,59 @@ static cudaError_t launch_sor(int n, const T* rho, T* phi, double coef, double o
     return cudaGetLastError();
 }
 
+// Inputs of a refined level's SOR problem (Sec. 2.3; reading R26), one
+// block per patch group: every cell of the 18^3 potential block -- the
+// one-cell ghost layer (Dirichlet data) and the interior (initial guess) --
+// by the Min-Mod interpolation of the coarser level's potential (the same
+// arithmetic as the ghost interpolation of the hydro gathers, on one
+// variable), and the group's density as a 16^3 block, both x fastest.
+constexpr int NT_PREP = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(NT_PREP) k_poisson_prepare(const PrepArgs<T> a) {
+    __shared__ int s_csrc[27], s_cmask[27];
+    const int g = blockIdx.x, t = threadIdx.x;
+    const int P = a.parent[g];
+    if (t < 27) region_entry(a.nbrc, P >> 3, t, s_csrc, s_cmask);
+    __syncthreads();
+    const int lp = P & 7;
+    const int px = lp & 1, py = (lp >> 1) & 1, pz = (lp >> 2) & 1;
+    constexpr int dd[7][3] = {{0, 0, 0}, {-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+    T* out = a.phi_blk + (size_t)g * PP * PP * PP;
+    for (int i = t; i < PP * PP * PP; i += NT_PREP) {
+        const int x = i % PP - 1, y = (i / PP) % PP - 1, z = i / (PP * PP) - 1;   // group-local, -1 .. 16
+        const int cx = PS * px + (x >> 1), cy = PS * py + (y >> 1), cz = PS * pz + (z >> 1);
+        T c[7];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            int xa = cx + dd[q][0], ya = cy + dd[q][1], za = cz + dd[q][2];
+            const int s = resolve(s_csrc, s_cmask, xa, ya, za);
+            c[q] = a.phi_c[cell_offset(s < 0 ? 0 : s, xa, ya, za)];   // s < 0 cannot pass host validation
+        }
+        const T sx = (x & 1) ? T(1) : T(-1), sy = (y & 1) ? T(1) : T(-1), sz = (z & 1) ? T(1) : T(-1);
+        const T U = c[0];
+        const T Sx = minmod_slope(c[1], U, c[2]);
+        const T Sy = minmod_slope(c[3], U, c[4]);
+        const T Sz = minmod_slope(c[5], U, c[6]);
+        const T tt = (sx * Sx + sy * Sy) + sz * Sz;
+        out[i] = U + T(0.25) * tt;
+    }
+    T* rb = a.rho_blk + (size_t)g * CELLS_PG;
+    for (int i = t; i < CELLS_PG; i += NT_PREP) {
+        const int x = i % GS, y = (i / GS) % GS, z = i / (GS * GS);
+        rb[i] = a.u[cell_offset(g, x, y, z)];
+    }
+}
+
+template <typename T>
+cudaError_t launch_poisson_prepare(const PrepArgs<T>& a, cudaStream_t st) {
+    if (a.n <= 0) return cudaSuccess;
+    k_poisson_prepare<T><<<a.n, NT_PREP, 0, st>>>(a);
+    return cudaGetLastError();
+}
+template cudaError_t launch_poisson_prepare<float>(const PrepArgs<float>&, cudaStream_t);
+template cudaError_t launch_poisson_prepare<double>(const PrepArgs<double>&, cudaStream_t);
+
 }  // namespace gh
 
 using namespace gh;
