@@ -138,32 +138,53 @@ static cudaError_t launch_sor(int n, const T* rho, T* phi, double coef, double o
 // variable), and the group's density as a 16^3 block, both x fastest.
 constexpr int NT_PREP = 256;
 
+// The coarse cells the group's interpolation reads -- its parent patch and
+// two coarse cells around it, 12^3 -- are staged in shared memory first (all
+// loads of a thread in flight together), so each fine cell then reads its
+// seven coarse values from shared memory.
+constexpr int CW = PS + 4;            // 12 coarse cells per axis
+
 template <typename T>
 __global__ void __launch_bounds__(NT_PREP) k_poisson_prepare(const PrepArgs<T> a) {
     __shared__ int s_csrc[27], s_cmask[27];
+    __shared__ T s_c[CW * CW * CW];
     const int g = blockIdx.x, t = threadIdx.x;
     const int P = a.parent[g];
     if (t < 27) region_entry(a.nbrc, P >> 3, t, s_csrc, s_cmask);
     __syncthreads();
     const int lp = P & 7;
     const int px = lp & 1, py = (lp >> 1) & 1, pz = (lp >> 2) & 1;
-    constexpr int dd[7][3] = {{0, 0, 0}, {-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+    const int ox = PS * px - 2, oy = PS * py - 2, oz = PS * pz - 2;   // coarse origin of the staged cube
+    constexpr int NS = CW * CW * CW;
+    constexpr int PER = (NS + NT_PREP - 1) / NT_PREP;
+    T v[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = k * NT_PREP + t;
+        if (i < NS) {
+            int xa = ox + i % CW, ya = oy + (i / CW) % CW, za = oz + i / (CW * CW);
+            // proper nesting puts the whole cube in existing coarse patches;
+            // a region that did not resolve would only be left unread
+            const int s = resolve(s_csrc, s_cmask, xa, ya, za);
+            v[k] = s < 0 ? T(0) : a.phi_c[cell_offset(s, xa, ya, za)];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = k * NT_PREP + t;
+        if (i < NS) s_c[i] = v[k];
+    }
+    __syncthreads();
     T* out = a.phi_blk + (size_t)g * PP * PP * PP;
     for (int i = t; i < PP * PP * PP; i += NT_PREP) {
         const int x = i % PP - 1, y = (i / PP) % PP - 1, z = i / (PP * PP) - 1;   // group-local, -1 .. 16
-        const int cx = PS * px + (x >> 1), cy = PS * py + (y >> 1), cz = PS * pz + (z >> 1);
-        T c[7];
-#pragma unroll
-        for (int q = 0; q < 7; ++q) {
-            int xa = cx + dd[q][0], ya = cy + dd[q][1], za = cz + dd[q][2];
-            const int s = resolve(s_csrc, s_cmask, xa, ya, za);
-            c[q] = a.phi_c[cell_offset(s < 0 ? 0 : s, xa, ya, za)];   // s < 0 cannot pass host validation
-        }
+        // the coarse cell (x >> 1, ...) of the parent patch, in the staged cube
+        const int c0 = (((z >> 1) + 2) * CW + ((y >> 1) + 2)) * CW + ((x >> 1) + 2);
+        const T U = s_c[c0];
+        const T Sx = minmod_slope(s_c[c0 - 1], U, s_c[c0 + 1]);
+        const T Sy = minmod_slope(s_c[c0 - CW], U, s_c[c0 + CW]);
+        const T Sz = minmod_slope(s_c[c0 - CW * CW], U, s_c[c0 + CW * CW]);
         const T sx = (x & 1) ? T(1) : T(-1), sy = (y & 1) ? T(1) : T(-1), sz = (z & 1) ? T(1) : T(-1);
-        const T U = c[0];
-        const T Sx = minmod_slope(c[1], U, c[2]);
-        const T Sy = minmod_slope(c[3], U, c[4]);
-        const T Sz = minmod_slope(c[5], U, c[6]);
         const T tt = (sx * Sx + sy * Sy) + sz * Sz;
         out[i] = U + T(0.25) * tt;
     }
