@@ -179,3 +179,26 @@ def test_prepare_rejects_level_zero():
     O = oracle.OracleLevels(H, _states(H))
     with pytest.raises(ValueError):
         O.poisson_prepare(0, np.zeros(1))
+
+
+@pytest.mark.parametrize("omega", [1.0, 1.5])
+def test_asymptotic_convergence_factor(omega):
+    """The red-black iteration on the 16^3 Dirichlet problem contracts the
+    error, asymptotically, by the spectral radius the theory of SOR gives
+    for consistently ordered matrices: with the Jacobi radius
+    mu = cos(pi / 17) of the 7-point Laplacian on 16 interior cells per
+    axis, lambda solves (lambda + omega - 1)^2 = lambda omega^2 mu^2, the
+    largest root being ((omega mu + sqrt(omega^2 mu^2 - 4 (omega - 1))) / 2)^2
+    below the optimal omega (mu^2 for Gauss-Seidel, omega = 1).  A wrong
+    colouring, weight or neighbour sum changes the rate."""
+    rng = np.random.default_rng(9)
+    phi = np.zeros((P, P, P))
+    phi[1:-1, 1:-1, 1:-1] = rng.standard_normal((N, N, N))
+    rho = np.zeros((N, N, N))
+    mu = np.cos(np.pi / (N + 1))
+    lam = ((omega * mu + np.sqrt(omega ** 2 * mu ** 2 - 4 * (omega - 1))) / 2) ** 2
+    k1, k2 = 150, 350
+    _, _, r1 = oracle.sor_group(phi, rho, 1.0, omega, k1, 0.0)
+    _, _, r2 = oracle.sor_group(phi, rho, 1.0, omega, k2, 0.0)
+    rate = (r2 / r1) ** (1.0 / (k2 - k1))
+    assert abs(rate - lam) < 2e-3, (rate, lam)
