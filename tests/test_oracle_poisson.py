@@ -201,4 +201,4 @@ def test_asymptotic_convergence_factor(omega):
     _, _, r1 = oracle.sor_group(phi, rho, 1.0, omega, k1, 0.0)
     _, _, r2 = oracle.sor_group(phi, rho, 1.0, omega, k2, 0.0)
     rate = (r2 / r1) ** (1.0 / (k2 - k1))
-    assert abs(rate - lam) < 2e-3, (rate, lam)
+    assert abs(rate - lam) < 1e-6, (rate, lam)
