@@ -795,8 +795,8 @@ def main():
     dist = None
     if world > 1:
         import torch.distributed as dist_mod
-        backend = "nccl" if args.impl == "ours" else "gloo"
-        dist_mod.init_process_group(backend=backend)
+        from paper_0907_3390_gb300 import replicas
+        replicas.init(dist_mod, "nccl" if args.impl == "ours" else "gloo")
         dist = dist_mod
     if args.impl == "reference":
         rc = run_reference(args, rank, world)

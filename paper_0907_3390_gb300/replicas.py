@@ -11,6 +11,16 @@ combine timings: no data moves between ranks.
 """
 from __future__ import annotations
 
+import datetime
+
+
+def init(dist, backend: str, timeout_s: float = 300.0) -> None:
+    """Join the process group (rank, world size and rendezvous from the
+    environment, as torchrun sets them) with a bounded timeout: a rank that
+    dies between steps makes the others' next barrier or reduction fail
+    with an error within timeout_s instead of waiting for ever."""
+    dist.init_process_group(backend=backend, timeout=datetime.timedelta(seconds=timeout_s))
+
 
 def world_size(dist) -> int:
     return 1 if dist is None else dist.get_world_size()

@@ -61,3 +61,37 @@ def test_one_process_is_its_own_job():
     assert R.max_over_ranks(3.5, None) == 3.5
     assert R.whole_job_rate(100.0, 0.5, None) == (200.0, 0.5)
     R.barrier(None)
+
+
+def _worker_dies(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    os.environ["RANK"] = str(rank)          # as torchrun sets them
+    os.environ["WORLD_SIZE"] = str(world)
+    R.init(dist, "gloo", timeout_s=5.0)
+    if rank == 1:
+        os._exit(0)                     # a rank that leaves between steps, without a word
+    import time
+    t0 = time.perf_counter()
+    try:
+        R.barrier(dist)
+        q.put(("no error", time.perf_counter() - t0))
+    except Exception as e:              # the failure surfaces on the host as an error
+        q.put((type(e).__name__, time.perf_counter() - t0))
+
+
+def test_dead_rank_is_detected_on_the_host():
+    """A rank that exits between steps: the other rank's next barrier ends
+    with an error within the process group's timeout (here 5 s), instead of
+    waiting for ever."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_dies, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    what, waited = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert what != "no error"
+    assert waited < 60.0, waited
