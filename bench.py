@@ -1,13 +1,16 @@
 #!/usr/bin/env python3
 """Benchmark of the relaxing-TVD patch-group hydro path on GB300.
 
-A step is one pass of the whole hot path over the workload: one sweep set
-of every patch group (ghost gather + x/y/z or z/y/x sweeps, fused in one
-persistent FP32 launch), then the diagnostics (CFL time step and the
-conservation / positivity check, FP64 reductions) whose dt feeds the next
-step.  The default workload is the periodic 128^3 smooth k^-2 random field
-(4096 patches of 8^3 = 512 patch groups).  It fits in L2, so L2 is flushed
-(a 256 MiB write) before every timed step, outside the timed interval.
+A step is one pass of the whole hot path over the workload: by default
+(--mode pair) one gamer_hydro_step_pair call, the xyz and the zyx sweep set
+of every patch group with one dt (ghost gather + x/y/z then z/y/x sweeps,
+two cell-updates per cell, one persistent FP32 launch for one level), then
+the diagnostics (CFL time step and the conservation / positivity check,
+FP64 reductions) whose dt feeds the next step; --mode step times single
+sweep sets (gamer_hydro_step).  The default workload is the periodic 128^3
+smooth k^-2 random field (4096 patches of 8^3 = 512 patch groups).  It fits
+in L2, so L2 is flushed (a 256 MiB write) before every timed step, outside
+the timed interval.
 
 Prints ONE JSON line (rank 0).  See --help for options.  ``--impl
 reference`` times the FP64 CPU oracle instead (on a bounded sample of the
