@@ -78,7 +78,10 @@ def lib():
             L.orc_cfl_dt.restype = C.c_double
             L.orc_cfl_dt.argtypes = [C.POINTER(_Level), C.c_int, C.c_double, C.c_double]
             L.orc_flag_level.argtypes = [C.POINTER(_Level), C.c_int, C.c_int, C.c_double, C.c_int, C.c_double,
-                                         C.c_int, C.c_int, C.POINTER(C.c_uint32)]
+                                         C.c_int, C.c_double, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                                         C.POINTER(C.c_int64)]
+            L.orc_flag_criterion.argtypes = [C.POINTER(_Level), C.c_int, C.c_int, C.c_double, C.c_int,
+                                             C.c_double, dp, dp]
             L.orc_refine_fill.argtypes = [C.POINTER(_Level), C.c_int, C.c_int, C.POINTER(C.c_int32),
                                           C.POINTER(C.c_int32), dp, C.c_int, dp]
             L.orc_gravity_level.argtypes = [dp, C.c_int, dp, C.c_double, C.c_double]
@@ -336,17 +339,41 @@ class OracleLevels:
         self._refresh()
         return lib().orc_level_max_speed(C.byref(self._arr[l]), gamma)
 
-    def flag_level(self, l: int, gamma: float, criterion: int, threshold: float, n_buffer: int,
-                   single: bool = False) -> np.ndarray:
-        """Per-patch flag-buffer masks of level l (orc_flag_level); single:
-        criteria in single precision (values must be single-precision numbers)."""
+    def flag_level(self, l: int, gamma: float, criterion: int, threshold: float, n_buffer: int) -> np.ndarray:
+        """Per-patch flag-buffer masks of level l (orc_flag_level), the
+        criterion decided in double precision."""
+        return self.flag_level_bounds(l, gamma, criterion, threshold, n_buffer, 0.0)[0]
+
+    def flag_level_bounds(self, l: int, gamma: float, criterion: int, threshold: float, n_buffer: int,
+                          u_eval: float):
+        """(masks of the cells flagged whatever the rounding, masks of the
+        cells that may be flagged, number of cells that may go either way)
+        when the criterion is evaluated in a format of unit roundoff u_eval
+        (orc_flag_level); u_eval = 0 gives the double decision twice."""
         self._refresh()
-        masks = np.zeros(8 * self.H.levels[l].n_groups, dtype=np.uint32)
-        r = lib().orc_flag_level(self._arr, self.n, l, gamma, criterion, threshold, n_buffer, 1 if single else 0,
-                                 masks.ctypes.data_as(C.POINTER(C.c_uint32)))
+        n = 8 * self.H.levels[l].n_groups
+        sure = np.zeros(n, dtype=np.uint32)
+        maybe = np.zeros(n, dtype=np.uint32)
+        near = C.c_int64(0)
+        r = lib().orc_flag_level(self._arr, self.n, l, gamma, criterion, threshold, n_buffer, float(u_eval),
+                                 sure.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                 maybe.ctypes.data_as(C.POINTER(C.c_uint32)), C.byref(near))
         if r != 0:
             raise ValueError(f"orc_flag_level: {r}")
-        return masks
+        return sure, maybe, int(near.value)
+
+    def flag_criterion(self, l: int, gamma: float, criterion: int, u_eval: float = 0.0):
+        """Per cell of level l ([8 n_groups][8][8][8]) the criterion value in
+        double precision and the bound on its error when evaluated at unit
+        roundoff u_eval (orc_flag_criterion)."""
+        self._refresh()
+        n = 8 * self.H.levels[l].n_groups
+        val = np.empty((n, 8, 8, 8))
+        bound = np.empty((n, 8, 8, 8))
+        r = lib().orc_flag_criterion(self._arr, self.n, l, gamma, criterion, float(u_eval), _dp(val), _dp(bound))
+        if r != 0:
+            raise ValueError(f"orc_flag_criterion: {r}")
+        return val, bound
 
     def refine_fill(self, l: int, parent_new, inherit, u_old) -> np.ndarray:
         """Data of a rebuilt level l+1 (orc_refine_fill) from this level's u."""

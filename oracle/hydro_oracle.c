@@ -588,136 +588,198 @@ int orc_level_fixup(const orc_level *lv, int n_levels, int l, double dt)
 /* ------------------------------------------------------------ regridding */
 
 /* Quantity of the refinement criterion at a group-local position (density
- * or pressure, Eqs. ShockTube_RefineCriterion and BlastWave_RefineCriterion):
- * 0 on success, 1 if the position only exists on the coarser level. */
-static int crit_value(const orc_level *L, int g, int x, int y, int z, int criterion, double gamma, double *q)
+ * or pressure, Eqs. ShockTube_RefineCriterion and BlastWave_RefineCriterion)
+ * and a first-order bound on the error of evaluating it in a binary format
+ * of unit roundoff u: |fl_u(q) - q| <= u * eq (+ O(u^2)).  With exact inputs
+ * the density is exact (eq = 0).  For the pressure of Eqs. ThermalEnergy and
+ * EOS, P = (gamma-1)(e - K) with K = rho (vx^2 + vy^2 + vz^2) / 2 and
+ * v = m / rho: each velocity carries one rounding, each square three, the
+ * sum of three non-negative squares five, the product with rho six, so
+ * |fl(K) - K| <= 6 u K; the subtraction adds u |e - K| and the two roundings
+ * of gamma - 1 and of the product add 2 u |P| / (gamma - 1).  eq takes
+ * (gamma-1)(8 K + 4 |e - K|), above the first-order (gamma-1)(6 K + 3 |e - K|),
+ * so that any order of the three-term sum stays inside it.
+ * Returns 0 on success, 1 if the position only exists on the coarser level. */
+static int crit_value(const orc_level *L, int g, int x, int y, int z, int criterion, double gamma, double *q,
+                      double *eq)
 {
     double u[NV];
     int r = level_fetch(L, L->u, g, x, y, z, u);
     if (r != 0)
         return r;
-    *q = criterion == 1 ? orc_pressure(u, gamma) : u[0];
-    return 0;
-}
-
-/* The same in single precision (the paper's GPU precision), for levels
- * whose values are single-precision numbers: every operation rounded to
- * float. */
-static int crit_value_f32(const orc_level *L, int g, int x, int y, int z, int criterion, double gamma, float *q)
-{
-    double u[NV];
-    int r = level_fetch(L, L->u, g, x, y, z, u);
-    if (r != 0)
-        return r;
-    const float rho = (float)u[0];
     if (criterion != 1) {
-        *q = rho;
+        *q = u[0];
+        *eq = 0.0;
         return 0;
     }
-    const float vx = (float)u[1] / rho, vy = (float)u[2] / rho, vz = (float)u[3] / rho;
-    const float eps = (float)u[4] - 0.5f * rho * (vx * vx + vy * vy + vz * vz);
-    *q = (float)(gamma - 1.0) * eps;
+    *q = orc_pressure(u, gamma);
+    const double rho = u[0];
+    const double vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho;
+    const double K = 0.5 * rho * (vx * vx + vy * vy + vz * vz);
+    *eq = (gamma - 1.0) * (8.0 * fabs(K) + 4.0 * fabs(u[4] - K));
     return 0;
 }
 
-/* Flag step of the refinement-map rebuild (Sec. 2.1 step 4; readings R21,
- * R22).  A cell of level l satisfies
- *   criterion 0: max over axes of |rho(+1) - rho(-1)| / (2 |rho|) >= threshold
- *                (the relative change of density across one cell width),
- *   criterion 1: the same for the pressure,
- *   criterion 2: rho > threshold,
- * where a neighbour that only exists on the coarser level is replaced by the
- * cell itself.  Around every such cell the flag buffer is the cube of
- * 1 + 2 n_buffer cells; masks[p] of patch p gets bit (dz+1)*9+(dy+1)*3+(dx+1)
- * for every patch at offset (dx,dy,dz) (bit 13: p itself) that the buffer of
- * one of its cells reaches.  0 <= n_buffer <= 8.  single != 0: the criterion
- * is evaluated in single precision on single-precision values (the flags of
- * a single-precision run), else in double. */
-int orc_flag_level(const orc_level *lv, int n_levels, int l, double gamma, int criterion,
-                   double threshold, int n_buffer, int single, uint32_t *masks)
+/* The criterion of one cell of level l (group-local position x, y, z of
+ * group g; readings R21):
+ *   criterion 0 / 1: r = max over the three axes of |q(+1) - q(-1)| / (2 |q|)
+ *                    for q = rho / P, a neighbour that only exists on the
+ *                    coarser level replaced by the cell itself, NaN ratios
+ *                    (0 / 0) skipped, 0 if all are;
+ *   criterion 2:     r = rho.
+ * *bound gets a first-order bound on the error of the same value evaluated
+ * in a format of unit roundoff u_eval, |fl_u(r) - r| <= bound: with
+ * n = |q+ - q-| and d = 2 |q0|, fl(n) = (n + dn)(1 + d1), fl(d) = d + dd and
+ * a rounded quotient give |fl(r) - r| <= u ((e+ + e-) / d + 2 r e0 / d + 2 r)
+ * per axis, and the largest of the per-axis values moves by at most the
+ * largest per-axis bound.  The bound is infinite when the denominator itself
+ * is not known to one part in four (u 2 e0 > d / 4), where a first-order
+ * bound says nothing, and 0 when u_eval is 0. */
+static int cell_criterion(const orc_level *L, int g, int x, int y, int z, int criterion, double gamma,
+                          double u_eval, double *val, double *bound)
 {
-    if (l < 0 || l >= n_levels || n_buffer < 0 || n_buffer > PS || criterion < 0 || criterion > 2)
+    double q0, e0;
+    if (crit_value(L, g, x, y, z, criterion == 2 ? 0 : criterion, gamma, &q0, &e0) != 0)
+        return ORC_ERR_MAP;
+    if (criterion == 2) {
+        *val = q0;
+        *bound = 0.0;
+        return ORC_OK;
+    }
+    const int c[3] = {x, y, z};
+    const double d = 2.0 * fabs(q0);
+    double rmax = 0.0, emax = 0.0;
+    for (int a = 0; a < 3; a++) {
+        double qm, qp, em, ep;
+        int m[3] = {c[0], c[1], c[2]}, pp[3] = {c[0], c[1], c[2]};
+        m[a] -= 1;
+        pp[a] += 1;
+        int rm = crit_value(L, g, m[0], m[1], m[2], criterion, gamma, &qm, &em);
+        int rp = crit_value(L, g, pp[0], pp[1], pp[2], criterion, gamma, &qp, &ep);
+        if (rm < 0 || rp < 0)
+            return ORC_ERR_MAP;
+        if (rm == 1) {
+            qm = q0;
+            em = e0;
+        }
+        if (rp == 1) {
+            qp = q0;
+            ep = e0;
+        }
+        double r = fabs(qp - qm) / d;
+        if (r > rmax)
+            rmax = r;
+        double ea = (ep + em) / d;
+        if (ea > emax)
+            emax = ea;
+    }
+    /* the r terms with the largest r bound those of every axis */
+    double b = u_eval * (emax + 2.0 * rmax * e0 / d + 2.0 * rmax);
+    if (u_eval > 0.0 && !(u_eval * 2.0 * e0 <= 0.25 * d))
+        b = INFINITY;
+    *val = rmax;
+    *bound = b;
+    return ORC_OK;
+}
+
+/* Per cell of level l the criterion value and the bound on its error at
+ * unit roundoff u_eval (cell_criterion), in the level's storage order
+ * [8 n_groups][8][8][8]. */
+int orc_flag_criterion(const orc_level *lv, int n_levels, int l, double gamma, int criterion, double u_eval,
+                       double *val, double *bound)
+{
+    if (l < 0 || l >= n_levels || criterion < 0 || criterion > 2)
         return ORC_ERR_ARG;
     const orc_level *L = &lv[l];
-    for (int p = 0; p < 8 * L->n_groups; p++)
-        masks[p] = 0u;
     for (int g = 0; g < L->n_groups; g++)
         for (int z = 0; z < GS; z++)
             for (int y = 0; y < GS; y++)
                 for (int x = 0; x < GS; x++) {
-                    int hit;
-                    int c[3] = {x, y, z};
-                    if (single) {
-                        float q0;
-                        if (crit_value_f32(L, g, x, y, z, criterion == 2 ? 0 : criterion, gamma, &q0) != 0)
-                            return ORC_ERR_MAP;
-                        if (criterion == 2) {
-                            hit = (double)q0 > threshold;
-                        } else {
-                            float rmax = 0.0f;
-                            for (int a = 0; a < 3; a++) {
-                                float qm, qp;
-                                int m[3] = {c[0], c[1], c[2]}, pp[3] = {c[0], c[1], c[2]};
-                                m[a] -= 1;
-                                pp[a] += 1;
-                                int rm = crit_value_f32(L, g, m[0], m[1], m[2], criterion, gamma, &qm);
-                                int rp = crit_value_f32(L, g, pp[0], pp[1], pp[2], criterion, gamma, &qp);
-                                if (rm < 0 || rp < 0)
-                                    return ORC_ERR_MAP;
-                                if (rm == 1)
-                                    qm = q0;
-                                if (rp == 1)
-                                    qp = q0;
-                                float r = fabsf(qp - qm) / (2.0f * fabsf(q0));
-                                if (r > rmax)
-                                    rmax = r;
-                            }
-                            hit = (double)rmax >= threshold;
-                        }
-                    } else {
-                        double q0;
-                        if (crit_value(L, g, x, y, z, criterion == 2 ? 0 : criterion, gamma, &q0) != 0)
-                            return ORC_ERR_MAP;
-                        if (criterion == 2) {
-                            hit = q0 > threshold;
-                        } else {
-                            double rmax = 0.0;
-                            for (int a = 0; a < 3; a++) {
-                                double qm, qp;
-                                int m[3] = {c[0], c[1], c[2]}, pp[3] = {c[0], c[1], c[2]};
-                                m[a] -= 1;
-                                pp[a] += 1;
-                                int rm = crit_value(L, g, m[0], m[1], m[2], criterion, gamma, &qm);
-                                int rp = crit_value(L, g, pp[0], pp[1], pp[2], criterion, gamma, &qp);
-                                if (rm < 0 || rp < 0)
-                                    return ORC_ERR_MAP;
-                                if (rm == 1)
-                                    qm = q0;
-                                if (rp == 1)
-                                    qp = q0;
-                                double r = fabs(qp - qm) / (2.0 * fabs(q0));
-                                if (r > rmax)
-                                    rmax = r;
-                            }
-                            hit = rmax >= threshold;
-                        }
-                    }
-                    if (!hit)
-                        continue;
-                    int lp = ((z / PS) * 2 + (y / PS)) * 2 + (x / PS);
-                    int pc[3] = {x % PS, y % PS, z % PS};
-                    int lo[3], hi[3];
-                    for (int a = 0; a < 3; a++) {
-                        lo[a] = pc[a] - n_buffer < 0 ? -1 : 0;
-                        hi[a] = pc[a] + n_buffer > PS - 1 ? 1 : 0;
-                    }
-                    uint32_t m = 0u;
-                    for (int dz = lo[2]; dz <= hi[2]; dz++)
-                        for (int dy = lo[1]; dy <= hi[1]; dy++)
-                            for (int dx = lo[0]; dx <= hi[0]; dx++)
-                                m |= 1u << ((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1));
-                    masks[8 * g + lp] |= m;
+                    size_t k = cell_index(L, g, 0, x, y, z);
+                    int r = cell_criterion(L, g, x, y, z, criterion, gamma, u_eval, &val[k], &bound[k]);
+                    if (r != ORC_OK)
+                        return r;
                 }
+    return ORC_OK;
+}
+
+/* Flag buffer of one flagged cell (reading R22): the bit of every patch
+ * offset (dx,dy,dz) that the cube of 1 + 2 n_buffer cells around the cell
+ * reaches, bit (dz+1)*9 + (dy+1)*3 + (dx+1), into the mask of its patch. */
+static void buffer_bits(int g, int x, int y, int z, int n_buffer, uint32_t *masks)
+{
+    int lp = ((z / PS) * 2 + (y / PS)) * 2 + (x / PS);
+    int pc[3] = {x % PS, y % PS, z % PS};
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; a++) {
+        lo[a] = pc[a] - n_buffer < 0 ? -1 : 0;
+        hi[a] = pc[a] + n_buffer > PS - 1 ? 1 : 0;
+    }
+    uint32_t m = 0u;
+    for (int dz = lo[2]; dz <= hi[2]; dz++)
+        for (int dy = lo[1]; dy <= hi[1]; dy++)
+            for (int dx = lo[0]; dx <= hi[0]; dx++)
+                m |= 1u << ((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1));
+    masks[8 * g + lp] |= m;
+}
+
+/* Flag step of the refinement-map rebuild (Sec. 2.1 step 4; readings R21,
+ * R22).  A cell of level l is flagged when its criterion value r
+ * (cell_criterion) reaches the threshold: r >= threshold for the gradient
+ * criteria 0 (density) and 1 (pressure), r > threshold for criterion 2
+ * (density).  Around every such cell the flag buffer (buffer_bits) marks
+ * the patches it reaches; masks[p] of patch p gets their bits (bit 13: p
+ * itself).  0 <= n_buffer <= 8.  The decision is taken in double precision
+ * on the level's values.
+ *
+ * u_eval > 0 asks, in addition, for the decisions that an evaluation of
+ * the criterion in a format of unit roundoff u_eval could take: a cell
+ * whose value lies within the error bound of cell_criterion of the
+ * threshold may go either way.  masks gets the flags of the cells flagged whatever the
+ * rounding, masks_maybe (may be NULL when u_eval == 0) those of the cells
+ * that may be flagged, and *n_near (may be NULL) the number of cells that
+ * may go either way.  u_eval == 0: the plain double decision in both. */
+int orc_flag_level(const orc_level *lv, int n_levels, int l, double gamma, int criterion, double threshold,
+                   int n_buffer, double u_eval, uint32_t *masks, uint32_t *masks_maybe, int64_t *n_near)
+{
+    if (l < 0 || l >= n_levels || n_buffer < 0 || n_buffer > PS || criterion < 0 || criterion > 2 ||
+        !(u_eval >= 0.0))
+        return ORC_ERR_ARG;
+    const orc_level *L = &lv[l];
+    for (int p = 0; p < 8 * L->n_groups; p++) {
+        masks[p] = 0u;
+        if (masks_maybe != NULL)
+            masks_maybe[p] = 0u;
+    }
+    int64_t near = 0;
+    for (int g = 0; g < L->n_groups; g++)
+        for (int z = 0; z < GS; z++)
+            for (int y = 0; y < GS; y++)
+                for (int x = 0; x < GS; x++) {
+                    double r, b;
+                    int rc = cell_criterion(L, g, x, y, z, criterion, gamma, u_eval, &r, &b);
+                    if (rc != ORC_OK)
+                        return rc;
+                    int hit = criterion == 2 ? r > threshold : r >= threshold;
+                    int sure = hit, maybe = hit;
+                    if (u_eval > 0.0) {
+                        if (criterion == 2) {
+                            sure = r - b > threshold;
+                            maybe = r + b > threshold;
+                        } else {
+                            sure = r - b >= threshold;
+                            maybe = r + b >= threshold;
+                        }
+                    }
+                    if (sure != maybe)
+                        near++;
+                    if (sure)
+                        buffer_bits(g, x, y, z, n_buffer, masks);
+                    if (maybe && masks_maybe != NULL)
+                        buffer_bits(g, x, y, z, n_buffer, masks_maybe);
+                }
+    if (n_near != NULL)
+        *n_near = near;
     return ORC_OK;
 }
 

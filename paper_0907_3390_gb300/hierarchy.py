@@ -138,37 +138,49 @@ def _patch_key(level_coords, lp):
     return (2 * level_coords[0] + px, 2 * level_coords[1] + py, 2 * level_coords[2] + pz)
 
 
+def patch_neighbours(level: LevelMap) -> np.ndarray:
+    """int64 [8 n_groups, 27]: for patch p and offset bit
+    b = (dz+1)*9 + (dy+1)*3 + (dx+1), the patch of the same level at offset
+    (dx, dy, dz) from p, found through the group map; column 13 is p itself,
+    -1 marks a region that exists only on the coarser level and -2 one
+    outside the domain (an outflow face)."""
+    n = level.n_groups
+    lp = np.arange(8)
+    loc = np.stack([lp & 1, (lp >> 1) & 1, lp >> 2], axis=1)                       # [8, 3]
+    offs = np.array([[b % 3 - 1, (b // 3) % 3 - 1, b // 9 - 1] for b in range(27)])  # [27, 3]
+    s = loc[:, None, :] + offs[None, :, :]                                          # [8, 27, 3]
+    go = np.where(s < 0, -1, np.where(s > 1, 1, 0))                                 # group offset
+    q = s - 2 * go                                                                  # patch in that group
+    lq = (q[..., 2] * 2 + q[..., 1]) * 2 + q[..., 0]                                # [8, 27]
+    gb = (go[..., 2] + 1) * 9 + (go[..., 1] + 1) * 3 + (go[..., 0] + 1)             # [8, 27]
+    nbr = np.asarray(level.nbr, dtype=np.int64).reshape(n, 26)
+    gt = np.concatenate([nbr[:, :13], np.arange(n, dtype=np.int64)[:, None], nbr[:, 13:]], axis=1)
+    h = gt[:, gb]                                                                   # [n, 8, 27]
+    return np.where(h >= 0, 8 * h + lq[None], h).reshape(8 * n, 27)
+
+
 def build_hierarchy(base_npg: tuple[int, int, int], score_fn, n_levels: int,
-                    targets=None, L: float = 1.0) -> Hierarchy:
-    """Build a periodic, properly nested hierarchy.
+                    targets=None, L: float = 1.0,
+                    bc: tuple[str, str, str] = ("periodic",) * 3) -> Hierarchy:
+    """Build a properly nested hierarchy over a base level with the given
+    boundaries.
 
     ``score_fn(level, centres)`` receives the cell centres [3][8n][8][8][8]
     of a level and returns a refinement score per patch (shape [8n]); a
     patch with a positive score asks for refinement.  A patch is eligible
-    only if its 26 same-level neighbours all exist (proper nesting).  When
+    only if its 26 same-level neighbours all exist (proper nesting; a region
+    outside the domain at an outflow face counts as present).  When
     ``targets`` is given, level l+1 is made of the children of the
     ``targets[l+1] // 8`` eligible patches with the highest scores.  Patch
     groups of the new level are numbered in the order of their parents."""
     nx, ny, nz = base_npg
-    lv0 = uniform_level(base_npg, dh=L / (GROUP * nx))
+    lv0 = uniform_level(base_npg, dh=L / (GROUP * nx), bc=bc)
     levels = [lv0]
     H = Hierarchy(levels=levels, base_npg=base_npg, L=L)
     for lev in range(n_levels - 1):
         cur = levels[-1]
-        ext_p = tuple(2 * e for e in cur.extent)   # extent in patches
-        lookup = {}
-        for g in range(cur.n_groups):
-            for lp in range(8):
-                lookup[_patch_key(cur.coords[g], lp)] = 8 * g + lp
         score = np.asarray(score_fn(lev, H.cell_centres(lev)), dtype=np.float64)
-        eligible = []
-        for p in range(8 * cur.n_groups):
-            g, lp = divmod(p, 8)
-            k = _patch_key(cur.coords[g], lp)
-            if all(((k[0] + dx) % ext_p[0], (k[1] + dy) % ext_p[1], (k[2] + dz) % ext_p[2]) in lookup
-                   for (dx, dy, dz) in DIRS):
-                eligible.append(p)
-        eligible = np.asarray(eligible, dtype=np.int64)
+        eligible = np.nonzero(np.all(patch_neighbours(cur) != -1, axis=1))[0]
         if targets is not None:
             want = int(targets[lev + 1]) // 8
             order = np.argsort(-score[eligible], kind="stable")
@@ -184,30 +196,24 @@ def build_hierarchy(base_npg: tuple[int, int, int], score_fn, n_levels: int,
 def refine_level(cur: LevelMap, refine) -> LevelMap:
     """The next finer level made of the children of the listed patches of
     ``cur`` (one patch group per refined patch, numbered in list order);
-    sets ``cur.child``.  Every refined patch must have its 26 same-level
-    neighbours (periodic wrap)."""
-    ext_p = tuple(2 * e for e in cur.extent)
-    lookup = {}
-    for g in range(cur.n_groups):
-        for lp in range(8):
-            lookup[_patch_key(cur.coords[g], lp)] = 8 * g + lp
-    refine = [int(p) for p in refine]
+    sets ``cur.child``.  The new group's neighbour in direction d is the
+    child group of the patch next to its parent in direction d (-1 if that
+    patch is not refined, -2 outside the domain).  Every refined patch must
+    have its 26 same-level neighbours."""
+    refine = np.asarray([int(p) for p in refine], dtype=np.int64)
     child = np.full(8 * cur.n_groups, -1, dtype=np.int32)
-    fine_coords = np.empty((len(refine), 3), dtype=np.int64)
-    for i, p in enumerate(refine):
-        child[p] = i
-        g, lp = divmod(p, 8)
-        fine_coords[i] = _patch_key(cur.coords[g], lp)
+    child[refine] = np.arange(len(refine), dtype=np.int32)
     cur.child = child
-    n_f = len(refine)
-    nbr = np.empty((n_f, 26), dtype=np.int32)
-    for i, p in enumerate(refine):
-        k = fine_coords[i]
-        for (dx, dy, dz) in DIRS:
-            q = ((k[0] + dx) % ext_p[0], (k[1] + dy) % ext_p[1], (k[2] + dz) % ext_p[2])
-            qp = lookup[q]
-            nbr[i, dir_index(dx, dy, dz)] = child[qp] if child[qp] >= 0 else -1
-    return LevelMap(n_groups=n_f, dh=cur.dh / 2, nbr=nbr, parent=np.asarray(refine, dtype=np.int32),
+    pn = patch_neighbours(cur)[refine]
+    pn = np.concatenate([pn[:, :13], pn[:, 14:]], axis=1)                           # [n_f, 26]
+    if np.any(pn == -1):
+        raise ValueError("refined patch without its 26 same-level neighbours")
+    nbr = np.where(pn >= 0, child[np.maximum(pn, 0)], pn).astype(np.int32)
+    g, lp = refine // 8, refine % 8
+    loc = np.stack([lp & 1, (lp >> 1) & 1, lp >> 2], axis=1)
+    fine_coords = (2 * np.asarray(cur.coords, dtype=np.int64)[g] + loc).reshape(len(refine), 3)
+    ext_p = tuple(2 * e for e in cur.extent)
+    return LevelMap(n_groups=len(refine), dh=cur.dh / 2, nbr=nbr, parent=refine.astype(np.int32),
                     coords=fine_coords, extent=ext_p)
 
 

@@ -21,10 +21,6 @@ import numpy as np
 from . import binding as B
 from . import hierarchy as hm
 
-# offset of mask bit b: (b % 3 - 1, (b // 3) % 3 - 1, b // 9 - 1)
-_BIT_OFFSETS = np.array([[b % 3 - 1, (b // 3) % 3 - 1, b // 9 - 1] for b in range(27)], dtype=np.int64)
-
-
 def patch_coords(level) -> np.ndarray:
     """[8 n_groups, 3] patch coordinates of a level (patch index order)."""
     lp = np.arange(8)
@@ -37,38 +33,23 @@ def _keys(c, ext):
 
 
 def flagged_patches(level, masks: np.ndarray) -> np.ndarray:
-    """bool [8 n_groups]: patches reached by a mask bit of their own or of a sibling."""
-    pc = patch_coords(level)
-    ext = np.array([2 * e for e in level.extent], dtype=np.int64)
-    keys = _keys(pc, ext)
-    order = np.argsort(keys)
-    out = np.zeros(len(pc), dtype=bool)
+    """bool [8 n_groups]: patches reached by a mask bit of their own or of a
+    sibling (mask bit b of patch p points at the patch at offset b of p;
+    bits that point outside the domain or off the level are dropped)."""
+    pn = hm.patch_neighbours(level)
+    out = np.zeros(pn.shape[0], dtype=bool)
     m = masks.astype(np.uint64)
     for b in range(27):
         src = np.nonzero((m >> np.uint64(b)) & np.uint64(1))[0]
-        if len(src) == 0:
-            continue
-        tgt = _keys((pc[src] + _BIT_OFFSETS[b]) % ext, ext)
-        pos = np.searchsorted(keys[order], tgt)
-        pos = np.minimum(pos, len(order) - 1)
-        hit = keys[order][pos] == tgt
-        out[order[pos[hit]]] = True
+        tgt = pn[src, b]
+        out[tgt[tgt >= 0]] = True
     return out
 
 
 def _nested(level) -> np.ndarray:
-    """bool [8 n_groups]: patches whose 26 same-level neighbours all exist."""
-    pc = patch_coords(level)
-    ext = np.array([2 * e for e in level.extent], dtype=np.int64)
-    keys = np.sort(_keys(pc, ext))
-    ok = np.ones(len(pc), dtype=bool)
-    for b in range(27):
-        if b == 13:
-            continue
-        k = _keys((pc + _BIT_OFFSETS[b]) % ext, ext)
-        pos = np.minimum(np.searchsorted(keys, k), len(keys) - 1)
-        ok &= keys[pos] == k
-    return ok
+    """bool [8 n_groups]: patches whose 26 same-level neighbours all exist
+    (a region outside the domain at an outflow face counts as present)."""
+    return np.all(hm.patch_neighbours(level) != -1, axis=1)
 
 
 def rebuild(S, D, criterion: int, thresholds, n_buffer: int, max_levels: int):

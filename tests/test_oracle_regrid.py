@@ -4,6 +4,10 @@ R21-R23).
 * flag masks against an independent numpy statement of the criteria
   (density / pressure gradient across one cell, density threshold) and of
   the flag buffer, on random and on tanh-front data;
+* the bound on the criterion's rounding error in single precision: every
+  float32 evaluation (three operation orders) lies within it, it is not
+  vacuous, and float masks at exact ties lie between the sure and the
+  possible masks;
 * buffer closed forms: n_buffer = 0 flags only the patch itself, n_buffer
   = 8 every sibling;
 * refinement fill: Min-Mod children conserve the parent cell and reproduce
@@ -25,7 +29,7 @@ from paper_0907_3390_gb300 import workloads as wl
 G = 5.0 / 3.0
 
 
-def numpy_masks(u, npg, criterion, thr, nb, bc=("periodic",) * 3):
+def numpy_masks(u, npg, criterion, thr, nb, bc=("periodic",) * 3, r_override=None):
     """Independent statement of the flag step on a single level given as a
     domain array u[5][nz][ny][nx]."""
     rho = u[0]
@@ -39,6 +43,8 @@ def numpy_masks(u, npg, criterion, thr, nb, bc=("periodic",) * 3):
         q = rho
     if criterion == 2:
         hit = rho > thr
+    elif r_override is not None:
+        hit = r_override >= thr
     else:
         r = np.zeros_like(q)
         for ax in range(3):
@@ -96,15 +102,95 @@ def test_flag_masks_outflow_front():
     assert np.count_nonzero(got) > 0
 
 
-def test_single_precision_flags_on_single_values():
-    # the float evaluation decides like the double one away from ties
-    u, npg = wl.lognormal_cells(32, seed=23, sigma=0.1)
+U32 = 2.0 ** -24     # unit roundoff of single precision
+
+
+def f32_criterion(u, criterion, order):
+    """The criterion of every cell of a periodic domain u[5][nz][ny][nx]
+    (values already single-precision numbers) evaluated in numpy float32,
+    with one of several operation orders, all algebraically the same."""
+    f = np.float32
+    w = [np.asarray(x, dtype=f) for x in u]
+    rho = w[0]
+    if criterion == 0:
+        q = rho
+    else:
+        gm1 = f(G - 1.0)
+        if order == 0:
+            vx, vy, vz = w[1] / rho, w[2] / rho, w[3] / rho
+            q = gm1 * (w[4] - f(0.5) * rho * (vx * vx + vy * vy + vz * vz))
+        elif order == 1:
+            vx, vy, vz = w[1] / rho, w[2] / rho, w[3] / rho
+            q = (w[4] - (f(0.5) * rho) * ((vz * vz + vy * vy) + vx * vx)) * gm1
+        else:
+            vx, vy, vz = w[1] / rho, w[2] / rho, w[3] / rho
+            q = gm1 * (w[4] - f(0.5) * (w[1] * vx + w[2] * vy + w[3] * vz))
+    n = np.zeros_like(q)
+    for a in range(3):
+        n = np.maximum(n, np.abs(np.roll(q, -1, a) - np.roll(q, 1, a)))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        r = n / (f(2) * np.abs(q))
+    return np.where(r > 0, r, f(0)).astype(np.float64)
+
+
+@pytest.mark.parametrize("criterion", [0, 1])
+def test_flag_error_bound_holds_for_float_evaluations(criterion):
+    """The oracle's bound on the criterion's rounding error at unit
+    roundoff u contains every single-precision evaluation, in three
+    operation orders, on rough data (lognormal density, velocities up to
+    a few times the sound speed, so that the pressure loses digits to
+    cancellation), and is tight to within two orders of magnitude."""
+    for seed, sigma in ((31, 0.5), (32, 1.5)):
+        u, npg = wl.lognormal_cells(32, seed=seed, sigma=sigma)
+        u[1:4] *= 3.0                    # faster flows: kinetic energy dominates e
+        u[4] += 0.5 * (u[1] ** 2 + u[2] ** 2 + u[3] ** 2) / u[0] * (1 - 1 / 9.0)
+        u32 = u.astype(np.float32).astype(np.float64)
+        O = oracle.OracleLevels(wl.uniform_hierarchy(npg), [hm.domain_to_patches(u32, npg)])
+        val, bound = O.flag_criterion(0, G, criterion, U32)
+        r64 = hm.patches_to_domain(val[None], npg)[0]
+        b = hm.patches_to_domain(bound[None], npg)[0]
+        ok = np.isfinite(b)
+        assert ok.mean() > 0.999
+        worst = 0.0
+        for order in (0, 1, 2) if criterion == 1 else (0,):
+            r32 = f32_criterion(u32, criterion, order)
+            err = np.abs(r32 - r64)
+            assert np.all(err[ok] <= b[ok]), (order, np.max(err[ok] / b[ok]))
+            worst = max(worst, float(np.max(err[ok] / np.maximum(b[ok], 1e-300))))
+        assert worst > 0.01, worst       # the bound is not vacuous
+
+
+def test_flag_bounds_contain_float_masks_at_ties():
+    """Thresholds placed exactly at single-precision criterion values (the
+    hardest ties): the masks of a float evaluation lie between the masks of
+    the cells flagged whatever the rounding and those that may be flagged,
+    the double decision too; only the tie cells may differ."""
+    u, npg = wl.lognormal_cells(32, seed=33, sigma=0.5)
+    u32 = u.astype(np.float32).astype(np.float64)
+    H = wl.uniform_hierarchy(npg)
+    O = oracle.OracleLevels(H, [hm.domain_to_patches(u32, npg)])
+    for crit in (0, 1):
+        r32 = f32_criterion(u32, crit, 0)
+        for thr in np.sort(r32.ravel())[-3:-400:-97]:
+            sure, maybe, near = O.flag_level_bounds(0, G, crit, float(thr), 1, U32)
+            exact = O.flag_level(0, G, crit, float(thr), 1)
+            _, m32 = numpy_masks(u32, npg, crit, float(thr), 1, r_override=r32)
+            for m in (m32, exact):
+                assert not np.any(m & ~maybe) and not np.any(sure & ~m)
+            assert near >= 1 and near < 50
+            s0, m0, n0 = O.flag_level_bounds(0, G, crit, float(thr), 1, 0.0)
+            assert np.array_equal(s0, exact) and np.array_equal(m0, exact) and n0 == 0
+
+
+def test_flag_density_threshold_has_no_ties():
+    # the density criterion compares a stored value: no rounding, no tie band
+    u, npg = wl.lognormal_cells(32, seed=34, sigma=0.5)
     u32 = u.astype(np.float32).astype(np.float64)
     O = oracle.OracleLevels(wl.uniform_hierarchy(npg), [hm.domain_to_patches(u32, npg)])
-    for crit, thr in ((0, 0.3), (1, 0.048), (2, 1.35)):
-        a = O.flag_level(0, G, crit, thr, 2, single=True)
-        b = O.flag_level(0, G, crit, thr, 2, single=False)
-        assert np.mean(a == b) > 0.95
+    thr = float(np.sort(u32[0].ravel())[-50])
+    sure, maybe, near = O.flag_level_bounds(0, G, 2, thr, 0, U32)
+    assert near == 0 and np.array_equal(sure, maybe)
+    assert np.array_equal(sure, O.flag_level(0, G, 2, thr, 0))
 
 
 def test_buffer_closed_forms():
@@ -243,3 +329,57 @@ def test_rebuild_after_a_step_conserves_composite_sums():
     On = oracle.OracleLevels(Hn, sn)
     s1, _ = On.check(G)
     assert np.all(np.abs(s1 - s0) / (np.abs(s0) + 1e-3) < 1e-12), (s1 - s0)
+
+
+def _geometry_nbr(fine, bc):
+    """Neighbour map of a level from its group coordinates alone: the group
+    at coords + d (wrapped on periodic axes), -2 past an outflow face, -1
+    where no group of the level sits."""
+    ext = fine.extent
+    pos = {tuple(int(v) for v in fine.coords[g]): g for g in range(fine.n_groups)}
+    out = np.empty((fine.n_groups, 26), dtype=np.int32)
+    for g in range(fine.n_groups):
+        k = [int(v) for v in fine.coords[g]]
+        j = 0
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    if (dx, dy, dz) == (0, 0, 0):
+                        continue
+                    q = [k[0] + dx, k[1] + dy, k[2] + dz]
+                    val = None
+                    for a in range(3):
+                        if q[a] < 0 or q[a] >= ext[a]:
+                            if bc[a] == "periodic":
+                                q[a] %= ext[a]
+                            else:
+                                val = -2
+                    out[g, j] = val if val is not None else pos.get(tuple(q), -1)
+                    j += 1
+    return out
+
+
+@pytest.mark.parametrize("bc", [("periodic",) * 3, ("outflow", "periodic", "outflow")])
+def test_refine_maps_against_geometry(bc):
+    """The oracle's rebuilt maps (a walk through the coarse neighbour map)
+    against the geometry of the group coordinates, over random sets of
+    properly nested patches on two successive levels."""
+    rng = np.random.default_rng(5)
+    H = wl.uniform_hierarchy((3, 2, 3), bc=bc)
+    cur = org._own_level(H.levels[0])
+    for lev in range(2):
+        pc = org.patch_coords(cur)
+        nested = [p for p in range(8 * cur.n_groups) if org.properly_nested(cur, p)]
+        assert nested
+        refine = sorted(rng.choice(nested, size=max(1, len(nested) // 2), replace=False).tolist())
+        fine, child = org.refine_maps(cur, refine)
+        assert np.array_equal(fine.nbr, _geometry_nbr(fine, bc))
+        for i, p in enumerate(refine):
+            assert tuple(int(v) for v in fine.coords[i]) == pc[p]
+            assert child[p] == i and fine.parent[i] == p
+        assert np.count_nonzero(child >= 0) == len(refine)
+        if bc[0] == "outflow":
+            assert np.any(fine.nbr == -2)
+        cur = fine
+    # a patch next to an unrefined region of the coarser level is not nested
+    assert not all(org.properly_nested(cur, p) for p in range(8 * cur.n_groups))
