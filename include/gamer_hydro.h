@@ -335,7 +335,10 @@ int gamer_hydro_diagnose(gamer_hydro_t h, const gamer_hierarchy_t *H, double cfl
 
 /* The CFL time step and the conservation / positivity check of
  * gamer_hydro_diagnose, without a handle and without allocating any device
- * memory.  The paper has no counterpart; this is for callers that cannot
+ * memory.  *dt_out is the shared-time-step dt of Eq. CFL, each level
+ * limited by its own dh (what gamer_hydro_diagnose returns for a handle in
+ * the default shared-time-step mode; a handle with individual time steps
+ * scales level l's limit by 2^l instead, so the two differ there).  The paper has no counterpart; this is for callers that cannot
  * call cudaMalloc -- a thread that must not synchronise the device (as
  * cudaMalloc/cudaFree may), code running inside a memory arena that owns
  * all of the GPU's memory, a periodic health check that must not disturb
@@ -347,14 +350,16 @@ int gamer_hydro_diagnose(gamer_hydro_t h, const gamer_hierarchy_t *H, double cfl
  * level's u, n_groups, dh, and child below the finest level) and the host
  * outputs (dt_out, sums, n_bad: any may be NULL); gamma and precision are
  * those of the data.  Work runs on cuda_stream (NULL: legacy stream) and
- * the call waits for it.  The first call on a device looks the scratch
- * address up (cudaGetSymbolAddress) for that device, so make that first
+ * the call waits for it.  Every call looks the scratch address up in the
+ * current device's context (cudaGetSymbolAddress, which allocates
+ * nothing), so the address stays right after a context reset; the first
+ * call on a device may load the library's device code, so make that first
  * call before any stream capture.  All calls in the process share the
  * scratch and each call rewrites every part it reads, so no state carries
  * over; calls that overlap on the GPU (other threads, other streams) race
  * on it and must be serialised by the caller.  Errors: GAMER_ERR_ARG,
- * GAMER_ERR_CUDA, GAMER_ERR_UNSUPPORTED (device index above 63); the
- * message is available from gamer_hydro_last_error(NULL) on this thread. */
+ * GAMER_ERR_CUDA; the message is available from
+ * gamer_hydro_last_error(NULL) on this thread. */
 int gamer_hydro_diagnose_noalloc(double gamma, int precision, const gamer_hierarchy_t *H,
                                  double cfl, void *cuda_stream, double *dt_out, double sums[5],
                                  int64_t *n_bad);

@@ -285,7 +285,10 @@ _version_counter = [0]
 class DeviceHierarchy:
     """A hierarchy snapshot on the device: maps as int32 tensors, per-level
     state tensors u / u_out ([5, 8n, 8, 8, 8], float32 or float64), and the
-    C structs that point at them.  ``swap()`` exchanges u and u_out."""
+    C structs that point at them.  ``swap()`` exchanges u and u_out.  The
+    output buffers (u_out and the face fluxes) start filled with NaN, so a
+    cell that a call fails to write never holds a plausible value;
+    ``poison()`` refills them."""
 
     def __init__(self, H, states, dtype, device="cuda", with_flux=False):
         import torch
@@ -297,7 +300,7 @@ class DeviceHierarchy:
         # states: host arrays, or device tensors of this dtype that are used as they are
         self.u = [s if (torch.is_tensor(s) and s.is_cuda and s.dtype == dtype and s.is_contiguous())
                   else torch.as_tensor(np.ascontiguousarray(s), dtype=dtype).to(self.device) for s in states]
-        self.u_out = [torch.empty_like(x) for x in self.u]
+        self.u_out = [torch.full_like(x, float("nan")) for x in self.u]
         self.nbr = [torch.as_tensor(np.ascontiguousarray(lv.nbr, dtype=np.int32)).to(self.device)
                     for lv in H.levels]
         self.parent = [None if lv.parent is None else
@@ -306,7 +309,7 @@ class DeviceHierarchy:
         self.child = [None if lv.child is None else
                       torch.as_tensor(np.ascontiguousarray(lv.child, dtype=np.int32)).to(self.device)
                       for lv in H.levels]
-        self.flux = [torch.zeros((lv.n_groups, 3, 3, 5, 16, 16), dtype=dtype, device=self.device)
+        self.flux = [torch.full((lv.n_groups, 3, 3, 5, 16, 16), float("nan"), dtype=dtype, device=self.device)
                      if (with_flux and n > 1) else None for lv in H.levels]
         _version_counter[0] += 1
         self.version = _version_counter[0]
@@ -339,6 +342,11 @@ class DeviceHierarchy:
     def swap(self):
         self.u, self.u_out = self.u_out, self.u
         self._refresh()
+
+    def poison(self):
+        """Fill the output buffers (u_out, caller-owned face fluxes) with NaN."""
+        for t in self.u_out + [f for f in self.flux if f is not None]:
+            t.fill_(float("nan"))
 
     def states(self):
         return [x.detach().double().cpu().numpy() for x in self.u]

@@ -10,12 +10,14 @@
 //
 // How: the per-group partial results that the diagnostics kernels need as
 // scratch live in one file-scope __device__ array of fixed size, shared by
-// every call in the process.  Its address is looked up once per device with
-// cudaGetSymbolAddress (host code may not use the array's name as a device
-// pointer) and handed to the kernels.
+// every call in the process.  Every call looks its address up on the
+// current device with cudaGetSymbolAddress (host code may not use the
+// array's name as a device pointer) and hands it to the kernels.  The
+// address is not cached: after cudaDeviceReset, or when the primary
+// context is released and created again, the module is loaded anew and an
+// address kept from before would dangle.
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "gamer_hydro.h"
@@ -42,21 +44,13 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
 namespace {
 
-constexpr int MAX_DEVICES = 64;
-std::mutex g_mu;
-void* g_scratch_ptr[MAX_DEVICES] = {nullptr};
-
-// Device address of the scratch array on the current device, looked up on
-// the first call for that device.
-cudaError_t scratch_address(int dev, unsigned char** out) {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = p;
-    }
-    *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+// Device address of the scratch array in the current device's context
+// (the lookup allocates nothing).
+cudaError_t scratch_address(unsigned char** out) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    *out = static_cast<unsigned char*>(p);
     return cudaSuccess;
 }
 
@@ -112,11 +106,8 @@ extern "C" int gamer_hydro_diagnose_noalloc(double gamma, int precision, const g
         return fail(GAMER_ERR_ARG, "gamer_hydro_diagnose_noalloc covers at most " +
                                        std::to_string(NOALLOC_MAX_GROUPS) + " patch groups per call (got " +
                                        std::to_string(total) + ")");
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess && (dev < 0 || dev >= MAX_DEVICES)) return fail(GAMER_ERR_UNSUPPORTED, "device index too large");
     unsigned char* base = nullptr;
-    if (e == cudaSuccess) e = scratch_address(dev, &base);
+    cudaError_t e = scratch_address(&base);
     if (e != cudaSuccess) return fail(GAMER_ERR_CUDA, std::string("scratch set-up: ") + cudaGetErrorString(e));
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     // Every entry the kernels read (items [0, total), levels [0, n_levels))

@@ -157,3 +157,38 @@ def test_withheld_mark_times_out_and_the_handle_recovers():
     assert e.value.code == B.GAMER_ERR_ARG
     S.close()
     R.close()
+
+
+def test_pair_against_oracle_at_bench_size():
+    """The benchmark's call on the benchmark's workload, compared with the
+    oracle directly: two gamer_hydro_step_pair calls on the 128^3 smooth
+    k^-2 fields (4096 patches, 512 groups: 3.4 items per SM and a ragged
+    last round), each against the oracle's xyz and zyx sets with the dt the
+    pair used, element by element: per field L1 <= 2e-6 and max <= 1e-4 of
+    the field's scale (FP32 arithmetic against FP64, two sweep sets), dt
+    within 2e-6 of the oracle's Eq. CFL on the same values.  The buffer the
+    xyz sets write is NaN-filled before every pair, so a cell left unwritten
+    poisons the zyx sets that read it."""
+    import oracle
+    H, st = wl.single_level(*wl.smooth_grf(128, seed=1001))
+    st32 = [np.asarray(s, dtype=np.float32).astype(np.float64) for s in st]
+    S = B.Solver(G, 0, B.GAMER_FP32)
+    D = B.DeviceHierarchy(H, st, torch.float32)
+    O = oracle.OracleLevels(H, st32)
+    for k in range(2):
+        O_dt = oracle.OracleLevels(H, [D.u[0].double().cpu().numpy()]).cfl_dt(G, 0.5)
+        D.poison()
+        B.gamer_hydro_step_pair(S.h, D, 0.5)
+        dt, _, _, n_bad = B.gamer_hydro_step_result(S.h)
+        assert n_bad == 0
+        assert abs(dt - O_dt) <= 2e-6 * O_dt, (k, dt, O_dt)
+        O.step(G, dt, 0)
+        O.step(G, dt, 1)
+        got = D.u[0].double().cpu().numpy()
+        ref = O.u[0]
+        d = np.abs(got - ref).reshape(5, -1)
+        scale = np.abs(ref).reshape(5, -1).max(1)
+        L1, mx = d.mean(1) / scale, d.max(1) / scale
+        assert np.all(np.isfinite(got))
+        assert L1.max() <= 2e-6 and mx.max() <= 1e-4, (k, L1, mx)
+    S.close()

@@ -49,6 +49,9 @@ def test_noalloc_matches_handle_diagnose_twice(prec, case):
     else:
         H, st = _amr()
     S = B.Solver(G, 0, prec[0])
+    # the no-handle call returns the shared-time-step dt of Eq. CFL: compare
+    # with a handle in that mode (individual time steps scale level l by 2^l)
+    B.gamer_hydro_set_time_steps(S.h, 0)
     D = B.DeviceHierarchy(H, st, prec[1])
     for call in range(2):
         torch.cuda.synchronize()
