@@ -64,6 +64,15 @@ def parse():
     p.add_argument("--gravity", action="store_true",
                    help="instead of timing steps: the gravity operator G on the workload's level 0 (HBM GB/s "
                         "per launch, FP32 and FP64) and one xyzGGzyx double step against the fused pair step")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the other north-star workloads (3-level AMR, 512^3) that the default run adds "
+                        "under 'configs'")
+    p.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
+                   help="with --quick: time the FP32 path (default) or the plain FP64 path (one sweep set per "
+                        "step through gamer_hydro_step); for profiling the FP64 kernel")
+    p.add_argument("--launch-groups", type=int, default=0,
+                   help="with --precision fp64: patch groups per kernel launch (gamer_hydro_set_launch_groups; "
+                        "1 = one group per launch; 0 = the library default)")
     p.add_argument("--accuracy", action="store_true",
                    help="instead of timing: per-field L1 / max error of the FP32 path against the FP64 path "
                         "(bit-identical to the FP64 oracle) on every workload, plus positivity and conservation")
@@ -151,6 +160,27 @@ def profile_per_cell(key="dram_bytes_per_cell", kernel="sweep_f32"):
     if d.get("source_sha") != kernel_source_sha() or key not in d:
         return None
     return float(d[key])
+
+
+FP64_PEAK_TF = 1.25       # nominal GB300 FP64 rate (TFLOP/s)
+
+
+def profile_fp64():
+    """FP64 floating-point operations per cell-update of the plain FP64
+    kernel (DADD + DMUL + 2 DFMA per thread, from an ncu capture of
+    k_pg_f64), if the capture was taken on the current FP64 kernel source."""
+    path = os.path.join(ROOT, "profiles", "sweep_f64_counters.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    h = hashlib.sha256()
+    for name in ("sweep_f64.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_0907_3390_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    if d.get("source_sha") != h.hexdigest()[:16]:
+        return None
+    return {"flops_per_cell": float(d["fp64_flops_per_cell"]), "source": "profiles/sweep_f64_counters.json"}
 
 
 class ClockSampler:
@@ -261,10 +291,74 @@ def run_reference(args, rank, world):
 
 # ------------------------------------------------------------ our arm
 
+def sweep_kernel_ms(B, torch, S, D, flush, K, pair, n_levels, cfl=None):
+    """Average device time of the sweep launches of one step, from events
+    the library records around them (gamer_hydro_set_profiling; such steps
+    launch directly, events cannot be timed inside graphs), L2 flushed
+    before each step.  A one-level pair is one launch; a multi-level pair
+    runs as two steps, so its two sweep sets are timed as two
+    gamer_hydro_step calls."""
+    cfl = CFL if cfl is None else cfl
+    kev = (_timing_event(torch), _timing_event(torch))
+    torch.cuda.synchronize()
+    B.gamer_hydro_set_profiling(S.h, kev[0], kev[1])
+    out = []
+    for k in range(K):
+        if pair and n_levels == 1:
+            flush.fill_(float(k))
+            B.gamer_hydro_step_pair(S.h, D, cfl)
+            torch.cuda.synchronize()
+            out.append(kev[0].elapsed_time(kev[1]))
+        else:
+            t = 0.0
+            for _ in range(2 if pair else 1):
+                flush.fill_(float(k))
+                B.gamer_hydro_step(S.h, D, cfl)
+                D.swap()
+                torch.cuda.synchronize()
+                t += kev[0].elapsed_time(kev[1])
+            out.append(t)
+    B.gamer_hydro_set_profiling(S.h, None, None)
+    return float(np.mean(out))
+
+
+
 def _timing_event(torch):
     e = torch.cuda.Event(enable_timing=True)
     e.record()          # materialise the underlying cudaEvent_t
     return e
+
+
+def run_fp64_quick(args):
+    """--quick --precision fp64: sweep sets of the plain FP64 path (one per
+    step, gamer_hydro_advance_all with a fixed dt), for profiling k_pg_f64."""
+    import torch
+    from paper_0907_3390_gb300 import binding as B
+    desc, make = WORKLOADS[args.workload]
+    H, st = make()
+    cells = sum(lv.n_groups for lv in H.levels) * 4096
+    S = B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP64)
+    if args.launch_groups > 0:
+        B.gamer_hydro_set_launch_groups(S.h, args.launch_groups)
+    D = B.DeviceHierarchy(H, st, torch.float64)
+    dt = B.gamer_hydro_cfl_dt(S.h, D, CFL)
+    for _ in range(args.warmup):
+        S.step(D, dt)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        S.step(D, dt)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"metric": METRIC, "value": cells / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                      "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": desc, "step": "one FP64 sweep set (gamer_hydro_advance_all)",
+                                 "groups_per_launch": args.launch_groups or "library default"}}), flush=True)
+    S.close()
+    return 0
 
 
 def run_ours(args, rank, world, dist):
@@ -327,17 +421,20 @@ def run_ours(args, rank, world, dist):
     step_ms = sum(a.elapsed_time(b) for a, b in ev)
 
     # the dominant kernel: the same steps again with profiling events around
-    # the sweep launch (launched directly, events cannot be timed in graphs)
-    kev = (_timing_event(torch), _timing_event(torch))
-    torch.cuda.synchronize()
-    B.gamer_hydro_set_profiling(S.h, kev[0], kev[1])
-    kern_ms = []
-    for s in range(args.steps):
-        flush.fill_(float(s))
-        step()
+    # the sweep launches
+    if individual:
+        kev = (_timing_event(torch), _timing_event(torch))
         torch.cuda.synchronize()
-        kern_ms.append(kev[0].elapsed_time(kev[1]))
-    B.gamer_hydro_set_profiling(S.h, None, None)
+        B.gamer_hydro_set_profiling(S.h, kev[0], kev[1])
+        kern_ms = []
+        for s in range(args.steps):
+            flush.fill_(float(s))
+            step()
+            torch.cuda.synchronize()
+            kern_ms.append(kev[0].elapsed_time(kev[1]))
+        B.gamer_hydro_set_profiling(S.h, None, None)
+    else:
+        kern_ms = [sweep_kernel_ms(B, torch, S, D, flush, args.steps, args.mode == "pair", len(H.levels))]
     value, t_max = R.whole_job_rate(updates * args.steps, step_ms / 1e3, dist, dev)
     res = {"value": value, "ms_per_step": 1e3 * t_max / args.steps, "sets_per_step": sets,
            "updates_per_step": updates, "time_steps": "individual" if individual else "uniform"}
@@ -387,6 +484,8 @@ def run_ours(args, rank, world, dist):
         extras["e2e"] = run_e2e(args, B, R, torch, H, st, dev, stream, updates, dist)
         if rank == 0:
             extras.update(run_extras(args, B, torch, H, st, cells, dev, stream, updates, world))
+        if rank == 0 and world == 1 and not args.no_configs:
+            extras["configs"] = run_configs(args, B, torch, dev, stream)
     S.close()
     return res, extras, cells, desc
 
@@ -494,7 +593,34 @@ def run_extras(args, B, torch, H, st, cells, dev, stream, updates, world):
     torch.cuda.synchronize()
     ms64 = e0.elapsed_time(e1) / n64
     out["fp64_plain"] = {"value": cells / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
-                         "note": "whole step, one thread block per patch group, FP64 throughout"}
+                         "note": "batched FP64 path: one sweep set per step (gamer_hydro_step), one thread block "
+                                 "per patch group and every group of the level in one launch, FP64 throughout; "
+                                 "this is not the one-group-per-launch layout (see fp64_per_launch)"}
+    # the plain layout: one patch group per kernel launch
+    B.gamer_hydro_set_launch_groups(S64.h, 1)
+    n1 = 2
+    B.gamer_hydro_advance_all(S64.h, D64, dt)
+    D64.swap()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(n1):
+        B.gamer_hydro_advance_all(S64.h, D64, dt)
+        D64.swap()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms1 = e0.elapsed_time(e1) / n1
+    n_groups = sum(lv.n_groups for lv in H.levels)
+    out["fp64_per_launch"] = {"value": cells / (ms1 / 1e3), "unit": UNIT, "ms_per_set": ms1,
+                              "launches_per_set": n_groups,
+                              "note": "plain FP64 path, one patch group per kernel launch "
+                                      "(gamer_hydro_set_launch_groups(h, 1)), one sweep set per call"}
+    f64 = profile_fp64()
+    if f64 is not None:
+        achieved = f64["flops_per_cell"] * cells / (ms64 / 1e3) / 1e12
+        out["fp64_plain"]["roofline"] = {
+            "bound": "fp64", "achieved": achieved, "peak": FP64_PEAK_TF, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TF, "peak_kind": "nominal GB300 FP64 (no measured FP64 peak)",
+            "flops_per_cell": f64["flops_per_cell"], "source": f64["source"]}
     out["l1_rel_err_fp32_vs_fp64"] = {"fields": ["rho", "mx", "my", "mz", "e"], "value": [float(x) for x in l1],
                                       "after": "one sweep set"}
     S64.close()
@@ -509,6 +635,85 @@ def run_extras(args, B, torch, H, st, cells, dev, stream, updates, world):
     rate1, sample1, secs1 = cpu_oracle_rate(H, st, max(1.0, args.cpu_seconds / 4), 1, max_groups=16)
     out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
                            "seconds": secs, "value_1core": rate1, "sample_1core": sample1}
+    return out
+
+
+# ------------------------------------------------------------ other workloads
+
+# the other spec workloads that fit one GPU, run after the main line:
+# (workload, timed pair steps)
+CONFIG_RUNS = (("amr3", 10), ("uniform512", 5))
+
+
+def run_configs(args, B, torch, dev, stream):
+    """The uneven 3-level AMR batch (uniform dt) and the 262,144-patch 512^3
+    batch, each with the main line's step (gamer_hydro_step_pair: xyz + zyx
+    with one dt, CFL dt and check), L2 flushed before every timed step; the
+    sweep kernels' own time from events around their launches; per-field L1
+    error of one FP32 pair against the FP64 path from the same state with the
+    same dt (worst level, relative to the field's largest magnitude)."""
+    hbm, peak_kind = measured_peaks()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {}
+    for name, K in CONFIG_RUNS:
+        desc, make = WORKLOADS[name]
+        t0 = time.perf_counter()
+        H, st = make()
+        gen_s = time.perf_counter() - t0
+        cells = sum(lv.n_groups for lv in H.levels) * 4096
+        updates = 2 * cells
+        S = B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP32, stream=stream)
+        D = B.DeviceHierarchy(H, st, torch.float32, device=dev)
+        for _ in range(3):
+            B.gamer_hydro_step_pair(S.h, D, CFL)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(dev.index or 0)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for k in range(K):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            B.gamer_hydro_step_pair(S.h, D, CFL)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        step_ms = sum(a.elapsed_time(b) for a, b in ev) / K
+        _, _, _, n_bad = B.gamer_hydro_step_result(S.h)
+        k_ms = sweep_kernel_ms(B, torch, S, D, flush, K, True, H.n_levels)
+        S.close()
+        del D
+        achieved = BYTES_PER_CELL_F32 * updates / (k_ms / 1e3) / 1e9
+        # accuracy of one pair against the FP64 path, same state and dt
+        S64 = B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP64, stream=stream)
+        D64 = B.DeviceHierarchy(H, st, torch.float64, device=dev)
+        dt = B.gamer_hydro_cfl_dt(S64.h, D64, CFL)
+        S32 = B.Solver(GAMMA, B.GAMER_LIMITER_VANLEER, B.GAMER_FP32, stream=stream)
+        D32 = B.DeviceHierarchy(H, st, torch.float32, device=dev)
+        for _ in range(2):
+            S64.step(D64, dt)
+            S32.step(D32, dt)
+        l1 = np.zeros(5)
+        for l in range(H.n_levels):
+            ref = D64.u[l].reshape(5, -1)
+            d = (D32.u[l].double().reshape(5, -1) - ref).abs()
+            scale = ref.abs().max(dim=1).values.clamp_min(1e-300)
+            l1 = np.maximum(l1, (d.mean(dim=1) / scale).cpu().numpy())
+        S64.close()
+        S32.close()
+        del D64, D32
+        torch.cuda.empty_cache()
+        out[name] = {
+            "workload": desc, "patches": cells // 512, "levels": H.n_levels, "cells": cells,
+            "value": updates / (step_ms / 1e3), "unit": UNIT, "ms_per_step": step_ms, "steps": K,
+            "kernel_ms": k_ms,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "peak_kind": f"{peak_kind} copy bandwidth",
+                         "kernel": "the step's sweep launches (k_sweep_pair for one level; k_sweep_f32 per sweep "
+                                   "set over all levels otherwise)"},
+            "l1_rel_err_fp32_vs_fp64": dict(zip(["rho", "mx", "my", "mz", "e"], [float(x) for x in l1])),
+            "l1_after": "one xyz + zyx pair with the FP64 path's dt",
+            "n_bad_cells": n_bad, "clocks": clk, "input_generation_s": gen_s,
+        }
+        del H, st
     return out
 
 
@@ -801,6 +1006,8 @@ def main():
         from paper_0907_3390_gb300 import replicas
         replicas.init(dist_mod, "nccl" if args.impl == "ours" else "gloo")
         dist = dist_mod
+    if args.quick and args.precision == "fp64" and args.impl == "ours":
+        return run_fp64_quick(args)
     if args.impl == "reference":
         rc = run_reference(args, rank, world)
         if dist is not None:
@@ -827,7 +1034,7 @@ def main():
             "n_bad_cells": res["n_bad"],
             "conservation_drift_rel": res["conservation_drift_rel"],
         }
-        for k in ("e2e", "cpu_baseline", "fp64_plain", "l1_rel_err_fp32_vs_fp64"):
+        for k in ("e2e", "cpu_baseline", "fp64_plain", "fp64_per_launch", "l1_rel_err_fp32_vs_fp64", "configs"):
             if k in extras:
                 line[k] = extras[k]
         if "fp64_plain" in extras:

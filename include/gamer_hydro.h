@@ -199,6 +199,16 @@ int gamer_hydro_step_pair(gamer_hydro_t h, const gamer_hierarchy_t *H, double cf
  * GAMER_ERR_ARG for group < -1. */
 int gamer_hydro_test_withhold(gamer_hydro_t h, int group);
 
+/* FP64 handles: at most n patch groups per kernel launch of a level's
+ * sweep set (default 2048; each launch runs one thread block per group).
+ * n = 1 gives the plain one-group-per-launch layout of the paper's solver
+ * loop (Sec. 3.1 launches N_g groups at a time), the baseline the batched
+ * kernels are compared with.  Results do not depend on n.  Waits for the
+ * handle's stream and drops its cached graphs.  GAMER_ERR_ARG for n < 1,
+ * GAMER_ERR_UNSUPPORTED for FP32 handles (one persistent launch covers
+ * every group). */
+int gamer_hydro_set_launch_groups(gamer_hydro_t h, int n);
+
 /* Time stepping of multi-level hierarchies (Sec. 2.1).
  * GAMER_TIME_STEPS_UNIFORM (default): one dt for every level, as the paper
  * does with self-gravity.  GAMER_TIME_STEPS_INDIVIDUAL: every level takes

@@ -28,7 +28,7 @@ EXPORTS = [
     "gamer_hydro_set_parity", "gamer_hydro_get_parity", "gamer_hydro_cfl_dt",
     "gamer_hydro_advance", "gamer_hydro_fixup", "gamer_hydro_advance_all",
     "gamer_hydro_check", "gamer_hydro_diagnose", "gamer_hydro_step", "gamer_hydro_step_pair",
-    "gamer_hydro_set_time_steps", "gamer_hydro_flag", "gamer_hydro_refine_fill", "gamer_poisson_sor",
+    "gamer_hydro_set_time_steps", "gamer_hydro_set_launch_groups", "gamer_hydro_flag", "gamer_hydro_refine_fill", "gamer_poisson_sor",
     "gamer_gravity_update", "gamer_hydro_test_withhold", "gamer_poisson_prepare",
     "gamer_hydro_step_result",
     "gamer_hydro_diagnose_noalloc", "gamer_hydro_tune", "gamer_hydro_get_config",
@@ -87,6 +87,7 @@ def load(build_if_needed: bool = True) -> C.CDLL:
         L.gamer_hydro_step.argtypes = [H, hp, C.c_double]
         L.gamer_hydro_step_pair.argtypes = [H, hp, C.c_double]
         L.gamer_hydro_set_time_steps.argtypes = [H, C.c_int]
+        L.gamer_hydro_set_launch_groups.argtypes = [H, C.c_int]
         L.gamer_hydro_flag.argtypes = [H, hp, C.c_int, C.c_int, C.c_double, C.c_int, vp]
         L.gamer_hydro_refine_fill.argtypes = [H, hp, C.c_int, C.c_int, vp, vp, vp, C.c_int, vp]
         L.gamer_poisson_sor.argtypes = [C.c_int, C.c_int, vp, vp, C.c_double, C.c_double, C.c_int, C.c_double,
@@ -183,6 +184,10 @@ def gamer_hydro_step(h, H, cfl: float) -> None:
 
 def gamer_hydro_set_time_steps(h, mode: int) -> None:
     _check(h, load().gamer_hydro_set_time_steps(h, mode))
+
+
+def gamer_hydro_set_launch_groups(h, n: int) -> None:
+    _check(h, load().gamer_hydro_set_launch_groups(h, int(n)))
 
 
 def gamer_hydro_flag(h, H, level: int, criterion: int, threshold: float, n_buffer: int, masks) -> None:

@@ -961,6 +961,20 @@ int gamer_hydro_test_withhold(gamer_hydro_t h, int group) {
     return GAMER_OK;
 }
 
+int gamer_hydro_set_launch_groups(gamer_hydro_t h, int n) {
+    if (!h) return GAMER_ERR_ARG;
+    if (n < 1) return fail(h, GAMER_ERR_ARG, "groups per launch must be >= 1");
+    if (h->precision != GAMER_FP64) return fail(h, GAMER_ERR_UNSUPPORTED, "groups per launch applies to FP64 handles");
+    if (n != h->f64_chunk) {
+        CK(h, cudaSetDevice(h->device));
+        if (h->stream) CK(h, cudaStreamSynchronize(h->stream));
+        else CK(h, cudaDeviceSynchronize());
+        h->f64_chunk = n;
+        drop_hierarchy(h);            // captured graphs hold the old launch sequence
+    }
+    return GAMER_OK;
+}
+
 int gamer_hydro_set_time_steps(gamer_hydro_t h, int mode) {
     if (!h) return GAMER_ERR_ARG;
     if (mode != GAMER_TIME_STEPS_UNIFORM && mode != GAMER_TIME_STEPS_INDIVIDUAL)

@@ -35,6 +35,8 @@ Workloads (sizes in cells; each 8^3 patch belongs to a 16^3 patch group):
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 from .hierarchy import (GROUP, PATCH, Hierarchy, LevelMap, build_hierarchy,
@@ -73,24 +75,50 @@ def grf(n: int, rng: np.random.Generator, index: float = -2.0) -> np.ndarray:
     return d
 
 
-def sample_periodic(field: np.ndarray, x, y, z, L: float = 1.0) -> np.ndarray:
-    """Trilinear interpolation of a periodic cell-centred field [nz][ny][nx]
-    at physical positions (x, y, z) in [0, L)^3 (input construction only)."""
-    n = field.shape[0]
-    out = 0.0
-    fx = x / L * n - 0.5
-    fy = y / L * n - 0.5
-    fz = z / L * n - 0.5
+def _sample_chunk(flat, n, fx, fy, fz):
     ix, iy, iz = np.floor(fx).astype(np.int64), np.floor(fy).astype(np.int64), np.floor(fz).astype(np.int64)
     tx, ty, tz = fx - ix, fy - iy, fz - iz
+    xs = (ix % n, (ix + 1) % n)
+    ys = (iy % n * n, (iy + 1) % n * n)
+    zs = (iz % n * (n * n), (iz + 1) % n * (n * n))
+    out = 0.0
     for dz in (0, 1):
         wz = tz if dz else 1.0 - tz
         for dy in (0, 1):
             wy = ty if dy else 1.0 - ty
+            zy = zs[dz] + ys[dy]
             for dx in (0, 1):
                 wx = tx if dx else 1.0 - tx
-                out = out + wx * wy * wz * field[(iz + dz) % n, (iy + dy) % n, (ix + dx) % n]
+                out = out + wx * wy * wz * np.take(flat, zy + xs[dx])
     return out
+
+
+def sample_periodic(field: np.ndarray, x, y, z, L: float = 1.0) -> np.ndarray:
+    """Trilinear interpolation of a periodic cell-centred field [nz][ny][nx]
+    at physical positions (x, y, z) in [0, L)^3 (input construction only).
+    Large requests are split into chunks evaluated on a thread pool; every
+    value is formed by the same operations in the same order either way."""
+    n = field.shape[0]
+    flat = np.ascontiguousarray(field).ravel()
+    x, y, z = np.broadcast_arrays(np.asarray(x, dtype=np.float64), np.asarray(y, dtype=np.float64),
+                                  np.asarray(z, dtype=np.float64))
+    shape = x.shape
+    fx = (x / L * n - 0.5).ravel()
+    fy = (y / L * n - 0.5).ravel()
+    fz = (z / L * n - 0.5).ravel()
+    m = fx.size
+    chunk = 1 << 20
+    if m <= chunk:
+        return np.asarray(_sample_chunk(flat, n, fx, fy, fz)).reshape(shape)
+    import concurrent.futures as cf
+    out = np.empty(m)
+
+    def one(a):
+        b = min(a + chunk, m)
+        out[a:b] = _sample_chunk(flat, n, fx[a:b], fy[a:b], fz[a:b])
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        list(ex.map(one, range(0, m, chunk)))
+    return out.reshape(shape)
 
 
 # ------------------------------------------------------ single-level inputs

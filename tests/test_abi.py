@@ -45,6 +45,7 @@ def test_null_handle_is_rejected():
     assert lib.gamer_hydro_destroy(None) == B.GAMER_OK
     assert lib.gamer_hydro_advance(None, None, 0, 0.1) == B.GAMER_ERR_ARG
     assert lib.gamer_hydro_cfl_dt(None, None, 0.5, None) == B.GAMER_ERR_ARG
+    assert lib.gamer_hydro_set_launch_groups(None, 1) == B.GAMER_ERR_ARG
 
 
 def test_struct_layouts_match_header():

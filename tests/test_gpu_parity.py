@@ -447,3 +447,29 @@ def test_every_tuned_configuration_is_bit_identical(tmp_path, prec):
             for a, b in zip(ref, out):
                 assert np.array_equal(a, b), cfg
         S.close()
+
+
+def test_fp64_groups_per_launch_do_not_change_results():
+    """gamer_hydro_set_launch_groups: one patch group per launch (the plain
+    layout), three per launch and the default batch give the same FP64
+    state bit for bit, single level and AMR; FP32 handles refuse it."""
+    cases = [wl.single_level(*wl.lognormal_cells(32, seed=1000)), amr_case()]
+    for H, st in cases:
+        outs = []
+        for n in (None, 1, 3):
+            S = B.Solver(G, 0, B.GAMER_FP64)
+            if n is not None:
+                B.gamer_hydro_set_launch_groups(S.h, n)
+            D = B.DeviceHierarchy(H, st, torch.float64)
+            S.run(D, 0.5, 4)
+            torch.cuda.synchronize()
+            outs.append(D.states())
+            S.close()
+        for o in outs[1:]:
+            for a, b in zip(outs[0], o):
+                assert np.array_equal(a, b)
+    S = B.Solver(G, 0, B.GAMER_FP32)
+    with pytest.raises(B.GamerError) as e:
+        B.gamer_hydro_set_launch_groups(S.h, 1)
+    assert e.value.code == B.GAMER_ERR_UNSUPPORTED
+    S.close()
