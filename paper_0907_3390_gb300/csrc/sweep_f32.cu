@@ -799,10 +799,17 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> 
             __syncthreads();
             if (tid < 11 * 32) {
                 sweep<ORDER, 1, LIM>(sm, lam, args.gamma, args.gm1, fg, 11 * 32);
+                if (ROWI && has_next) {
+                    // coarse-fine rows make the gather pool long: the sweeping
+                    // warps take what is left of it once the tables are built
+                    asm volatile("bar.sync 2, 512;" ::: "memory");
+                    gather_pool<ORDER, 0, ROWI>(sm, args, nxt, &s_cnt[0]);
+                }
             } else if (has_next) {
                 build_tab(nxt, args, next, 11 * 32);
                 if (tid == 11 * 32) prefetch_item(args, next);
                 asm volatile("bar.sync 1, 160;" ::: "memory");      // warps 11..15: tables ready
+                if (ROWI) asm volatile("bar.arrive 2, 512;" ::: "memory");
                 gather_pool<ORDER, 0, ROWI>(sm, args, nxt, &s_cnt[0]);
             }
             __syncthreads();
@@ -812,6 +819,7 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> 
                     s_item[0] = next;
                     s_item[1] = has_next ? atomicAdd(args.queue, 1) : next;
                 }
+                if (ROWI && has_next) gather_pool<ORDER, 1, ROWI>(sm, args, nxt, &s_cnt[1]);
             } else if (has_next) {
                 gather_pool<ORDER, 1, ROWI>(sm, args, nxt, &s_cnt[1]);
             }
