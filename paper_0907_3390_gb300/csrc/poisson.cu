@@ -140,14 +140,17 @@ constexpr int NT_PREP = 256;
 
 // The coarse cells the group's interpolation reads -- its parent patch and
 // two coarse cells around it, 12^3 -- are staged in shared memory first (all
-// loads of a thread in flight together), so each fine cell then reads its
-// seven coarse values from shared memory.
+// loads of a thread in flight together).  The limited slopes of the 10^3
+// coarse cells whose children fill the block are then formed once per coarse
+// cell, and every fine cell reads its coarse value and three slopes.
 constexpr int CW = PS + 4;            // 12 coarse cells per axis
+constexpr int CF = PS + 2;            // 10 coarse cells per axis with children in the block
 
 template <typename T>
 __global__ void __launch_bounds__(NT_PREP) k_poisson_prepare(const PrepArgs<T> a) {
     __shared__ int s_csrc[27], s_cmask[27];
     __shared__ T s_c[CW * CW * CW];
+    __shared__ T s_sl[3][CF * CF * CF];
     const int g = blockIdx.x, t = threadIdx.x;
     const int P = a.parent[g];
     if (t < 27) region_entry(a.nbrc, P >> 3, t, s_csrc, s_cmask);
@@ -175,23 +178,40 @@ __global__ void __launch_bounds__(NT_PREP) k_poisson_prepare(const PrepArgs<T> a
         if (i < NS) s_c[i] = v[k];
     }
     __syncthreads();
+    // slopes of the coarse cells -1 .. 8 of the parent patch (cube index + 2)
+    for (int i = t; i < CF * CF * CF; i += NT_PREP) {
+        const int cx = i % CF, cy = (i / CF) % CF, cz = i / (CF * CF);
+        const int c0 = ((cz + 1) * CW + (cy + 1)) * CW + (cx + 1);
+        const T U = s_c[c0];
+        s_sl[0][i] = minmod_slope(s_c[c0 - 1], U, s_c[c0 + 1]);
+        s_sl[1][i] = minmod_slope(s_c[c0 - CW], U, s_c[c0 + CW]);
+        s_sl[2][i] = minmod_slope(s_c[c0 - CW * CW], U, s_c[c0 + CW * CW]);
+    }
+    __syncthreads();
     T* out = a.phi_blk + (size_t)g * PP * PP * PP;
     for (int i = t; i < PP * PP * PP; i += NT_PREP) {
         const int x = i % PP - 1, y = (i / PP) % PP - 1, z = i / (PP * PP) - 1;   // group-local, -1 .. 16
-        // the coarse cell (x >> 1, ...) of the parent patch, in the staged cube
-        const int c0 = (((z >> 1) + 2) * CW + ((y >> 1) + 2)) * CW + ((x >> 1) + 2);
-        const T U = s_c[c0];
-        const T Sx = minmod_slope(s_c[c0 - 1], U, s_c[c0 + 1]);
-        const T Sy = minmod_slope(s_c[c0 - CW], U, s_c[c0 + CW]);
-        const T Sz = minmod_slope(s_c[c0 - CW * CW], U, s_c[c0 + CW * CW]);
+        // the coarse cell (x >> 1, ...) of the parent patch
+        const int cx = (x >> 1) + 1, cy = (y >> 1) + 1, cz = (z >> 1) + 1;
+        const int cf = (cz * CF + cy) * CF + cx;
+        const T U = s_c[((cz + 1) * CW + (cy + 1)) * CW + (cx + 1)];
+        const T Sx = s_sl[0][cf], Sy = s_sl[1][cf], Sz = s_sl[2][cf];
         const T sx = (x & 1) ? T(1) : T(-1), sy = (y & 1) ? T(1) : T(-1), sz = (z & 1) ? T(1) : T(-1);
         const T tt = (sx * Sx + sy * Sy) + sz * Sz;
         out[i] = U + T(0.25) * tt;
     }
+    // density block, x fastest: the group's cells read in their storage order
+    // four at a time (one aligned quad of a patch row) and written as a quad
     T* rb = a.rho_blk + (size_t)g * CELLS_PG;
-    for (int i = t; i < CELLS_PG; i += NT_PREP) {
-        const int x = i % GS, y = (i / GS) % GS, z = i / (GS * GS);
-        rb[i] = a.u[cell_offset(g, x, y, z)];
+    const T* ug = a.u + ((size_t)g << 12);
+    for (int j = 4 * t; j < CELLS_PG; j += 4 * NT_PREP) {
+        const int patch = j >> 9, w = j & 511;
+        const int x = ((patch & 1) << 3) | (w & 7);
+        const int y = (((patch >> 1) & 1) << 3) | ((w >> 3) & 7);
+        const int z = ((patch >> 2) << 3) | (w >> 6);
+        T* d = rb + (z * GS + y) * GS + x;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d[q] = ug[j + q];
     }
 }
 
