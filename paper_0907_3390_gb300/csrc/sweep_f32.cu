@@ -733,13 +733,17 @@ constexpr int NT_F32 = 512;
 
 template <int ORDER, int LIM, bool ROWI = false>
 __device__ __forceinline__ void sweep_first(float* sm, const SweepArgs<float>& a, const ItemTab& t,
-                                            float lam, float* flux_g) {
+                                            float lam, float* flux_g, bool whole = false) {
     if (ORDER == 0) {
-        // x-rows (yp, zp); rows with yp in [3,19) get their centre first
+        // x-rows (yp, zp); rows with yp in [3,19) get their centre first --
+        // with `whole` (the first item of a CTA, nothing gathered before)
+        // every thread gathers its entire row: the x-sweep of a row reads
+        // that row only, so no barrier has to wait for the others
         const int c = threadIdx.x;
         if (c >= PD * PD) return;
         const int yp = c % PD, zp = c / PD;
-        if (yp >= NG && yp < NG + GS) gather_row<1, ROWI>(sm, a, t, yp, zp);
+        if (whole) gather_row<3, ROWI>(sm, a, t, yp, zp);
+        else if (yp >= NG && yp < NG + GS) gather_row<1, ROWI>(sm, a, t, yp, zp);
         float* p = sm + yp * XP + zp * (PD * XP);
         float* fl = nullptr;
         if (flux_g != nullptr && yp >= NG && yp < NG + GS && zp >= NG && zp < NG + GS)
@@ -773,15 +777,12 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> 
     do {
         if (s_item[0] >= args.total) break;
         int slot = 0;
+        bool first = true;
         build_tab(tab[0], args, s_item[0], 0);
         __syncthreads();
-        // the first item whole, except what sweep 1 loads itself (xyz: the
-        // centres of the rows with yp in [3,19))
-        for (int r = tid; r < PD * PD; r += NT_F32) {
-            const int yp = r % PD, zp = r / PD;
-            if (ORDER == 0 && yp >= NG && yp < NG + GS) gather_row<2, ROWI>(sm, args, tab[0], yp, zp);
-            else gather_row<3, ROWI>(sm, args, tab[0], yp, zp);
-        }
+        // the first item whole (xyz: in sweep 1, each thread its own row)
+        if (ORDER == 1)
+            for (int r = tid; r < PD * PD; r += NT_F32) gather_row<3, ROWI>(sm, args, tab[0], r % PD, r / PD);
 
         for (;;) {
             __syncthreads();
@@ -795,7 +796,8 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> 
             const int cur_item = cur.item;
             const int cur_g = cur.g;
 
-            sweep_first<ORDER, LIM, ROWI>(sm, args, cur, lam, fg);
+            sweep_first<ORDER, LIM, ROWI>(sm, args, cur, lam, fg, first);
+            first = false;
             __syncthreads();
             if (tid < 11 * 32) {
                 sweep<ORDER, 1, LIM>(sm, lam, args.gamma, args.gm1, fg, 11 * 32);
@@ -922,15 +924,10 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_pair(const SweepArgs<float>
     do {
         if (s_item[0] >= total) break;
         int slot = 0;
+        bool first = true;               // an xyz first item gathers its rows in sweep 1
         build_tab(tab[0], args, s_item[0], 0);
         __syncthreads();
-        if (tab[0].level == 0) {
-            for (int r = tid; r < PD * PD; r += NT_F32) {
-                const int yp = r % PD, zp = r / PD;
-                if (yp >= NG && yp < NG + GS) gather_row<2>(sm, args, tab[0], yp, zp);
-                else gather_row<3>(sm, args, tab[0], yp, zp);
-            }
-        } else {
+        if (tab[0].level != 0) {
             if (tid < 32) wait_inputs(args, tab[0].g, target);
             __syncthreads();
             for (int r = tid; r < PD * PD; r += NT_F32) gather_row<3>(sm, args, tab[0], r % PD, r / PD);
@@ -947,8 +944,9 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_pair(const SweepArgs<float>
             const float lam = cur.lam;
             const int cur_g = cur.g;
 
-            if (ord == 0) sweep_first<0, LIM>(sm, args, cur, lam, nullptr);
+            if (ord == 0) sweep_first<0, LIM>(sm, args, cur, lam, nullptr, first);
             else sweep_first<1, LIM>(sm, args, cur, lam, nullptr);
+            first = false;
             __syncthreads();
             if (tid == 11 * 32 && s_aux[0] >= 0) {
                 publish(args, s_aux[0], target);       // the previous xyz item

@@ -4,7 +4,9 @@ plain FP64 path, then the fix-ups and the diagnostics).
 
 * 512^3 uniform lognormal (262,144 patches): one step; sampled patch groups
   recomputed by the oracle one by one (its patch-group form reads only the
-  neighbourhood of each group).
+  neighbourhood of each group); and the benchmark's pair call, sampled
+  groups against the oracle's xyz sets of their neighbourhoods followed by
+  their zyx sets.
 * three-level AMR hierarchy over a 128^3 base (4096 / 9000 / 21000
   patches): two steps, every cell compared.
 * four-level stress hierarchies (32,768 patches): lognormal sigma 2.5 with
@@ -14,7 +16,7 @@ plain FP64 path, then the fix-ups and the diagnostics).
 Tolerances: FP64 bit-identical (and <= 1e-12 relative); FP32 per-field L1
 and max relative to the field's scale, two steps: L1 <= 1e-7 and max <=
 1e-5 (max <= 1e-3 in the Sedov case, whose blast cell starts 1e11 times
-hotter than its surroundings); one 512^3 step: L1 <= 2e-6, max <= 1e-4.
+hotter than its surroundings); one 512^3 step or pair: L1 <= 2e-6, max <= 1e-4.
 """
 import numpy as np
 import pytest
@@ -76,6 +78,39 @@ def test_uniform512_sampled_groups(uniform512, prec):
         assert np.array_equal(out, ref)
     else:
         assert L1.max() <= 2e-6 and mx.max() <= 1e-4, (L1, mx)
+    S.close()
+
+
+def test_uniform512_pair_sampled_groups(uniform512):
+    """The call the benchmark times on this workload (gamer_hydro_step_pair:
+    the xyz and the zyx set of every group in one FP32 launch, a group's zyx
+    set reading its neighbours' xyz results as they are published) against
+    the oracle on sampled groups: the oracle's xyz set of every group in
+    the sampled groups' neighbourhoods, then its zyx set of the sampled
+    groups, with the dt the pair used.  The buffer of the xyz results is
+    NaN-filled first, so a zyx set that read an unwritten neighbour fails."""
+    H, st = uniform512
+    n = H.levels[0].n_groups
+    S = B.Solver(G, B.GAMER_LIMITER_VANLEER, B.GAMER_FP32)
+    D = B.DeviceHierarchy(H, st, torch.float32)
+    D.poison()
+    B.gamer_hydro_step_pair(S.h, D, CFL)
+    dt, _, _, n_bad = B.gamer_hydro_step_result(S.h)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(11)
+    groups = np.unique(np.concatenate([[0, 1, n // 2, n - 1], rng.integers(0, n, 12)])).astype(np.int32)
+    nbr = np.asarray(H.levels[0].nbr)
+    hood = np.unique(np.concatenate([groups, nbr[groups].ravel()])).astype(np.int32)
+    src = st[0].astype(np.float32).astype(np.float64)
+    O1 = oracle.OracleLevels(H, [src], with_flux=False)
+    O1.advance_level(0, G, dt, 0, groups=hood)              # xyz sets of the neighbourhoods
+    O2 = oracle.OracleLevels(H, [O1.u_out[0]], with_flux=False)
+    O2.advance_level(0, G, dt, 1, groups=groups)            # zyx sets of the sampled groups
+    out = D.u[0].reshape(5, n, 8, 8, 8, 8)[:, groups].double().cpu().numpy()
+    ref = O2.u_out[0].reshape(5, n, 8, 8, 8, 8)[:, groups]
+    assert np.all(np.isfinite(out))
+    L1, mx = rel(out, ref)
+    assert L1.max() <= 2e-6 and mx.max() <= 1e-4, (L1, mx)
     S.close()
 
 
