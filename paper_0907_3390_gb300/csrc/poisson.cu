@@ -136,7 +136,7 @@ static cudaError_t launch_sor(int n, const T* rho, T* phi, double coef, double o
 // by the Min-Mod interpolation of the coarser level's potential (the same
 // arithmetic as the ghost interpolation of the hydro gathers, on one
 // variable), and the group's density as a 16^3 block, both x fastest.
-constexpr int NT_PREP = 256;
+constexpr int NT_PREP = 384;          // one thread per (x, y) of an 18 x 18 plane of the block
 
 // The coarse cells the group's interpolation reads -- its parent patch and
 // two coarse cells around it, 12^3 -- are staged in shared memory first (all
@@ -188,17 +188,24 @@ __global__ void __launch_bounds__(NT_PREP) k_poisson_prepare(const PrepArgs<T> a
         s_sl[2][i] = minmod_slope(s_c[c0 - CW * CW], U, s_c[c0 + CW * CW]);
     }
     __syncthreads();
+    // thread t < 18^2 fills column (x, y) = (t % 18 - 1, t / 18 - 1) of the
+    // block plane by plane (group-local coordinates -1 .. 16); the coarse
+    // cell of a fine cell is (x >> 1, ...) of the parent patch
     T* out = a.phi_blk + (size_t)g * PP * PP * PP;
-    for (int i = t; i < PP * PP * PP; i += NT_PREP) {
-        const int x = i % PP - 1, y = (i / PP) % PP - 1, z = i / (PP * PP) - 1;   // group-local, -1 .. 16
-        // the coarse cell (x >> 1, ...) of the parent patch
-        const int cx = (x >> 1) + 1, cy = (y >> 1) + 1, cz = (z >> 1) + 1;
-        const int cf = (cz * CF + cy) * CF + cx;
-        const T U = s_c[((cz + 1) * CW + (cy + 1)) * CW + (cx + 1)];
-        const T Sx = s_sl[0][cf], Sy = s_sl[1][cf], Sz = s_sl[2][cf];
-        const T sx = (x & 1) ? T(1) : T(-1), sy = (y & 1) ? T(1) : T(-1), sz = (z & 1) ? T(1) : T(-1);
-        const T tt = (sx * Sx + sy * Sy) + sz * Sz;
-        out[i] = U + T(0.25) * tt;
+    if (t < PP * PP) {
+        const int x = t % PP - 1, y = t / PP - 1;
+        const int cx = (x >> 1) + 1, cy = (y >> 1) + 1;
+        const T sx = (x & 1) ? T(1) : T(-1), sy = (y & 1) ? T(1) : T(-1);
+#pragma unroll 2
+        for (int zz = 0; zz < PP; ++zz) {
+            const int z = zz - 1, cz = (z >> 1) + 1;
+            const int cf = (cz * CF + cy) * CF + cx;
+            const T U = s_c[((cz + 1) * CW + (cy + 1)) * CW + (cx + 1)];
+            const T Sx = s_sl[0][cf], Sy = s_sl[1][cf], Sz = s_sl[2][cf];
+            const T sz = (z & 1) ? T(1) : T(-1);
+            const T tt = (sx * Sx + sy * Sy) + sz * Sz;
+            out[zz * PP * PP + t] = U + T(0.25) * tt;
+        }
     }
     // density block, x fastest: the group's cells read in their storage order
     // four at a time (one aligned quad of a patch row) and written as a quad
