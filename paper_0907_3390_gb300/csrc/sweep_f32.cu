@@ -665,11 +665,13 @@ __device__ __forceinline__ void sweep_last_store(float* sm, float lam, float g, 
     if (diag) acc.park(red);
 }
 
-// Combine the parked warp results of one item (threads 0..5) and write the
-// item's diagnostics: per-variable FP64 sums, the speed maximum as the bit
+// Combine the parked warp results of one item (threads t0..t0+5) and write
+// the item's diagnostics: per-variable FP64 sums, the speed maximum as the bit
 // pattern of a double, the bad-cell count.
-__device__ __forceinline__ void finish_diag(const DiagSink& d, int item, const float* red, int nwarps) {
-    const int t = threadIdx.x;
+__device__ __forceinline__ void finish_diag(const DiagSink& d, int item, const float* red, int nwarps,
+                                            int t0 = 0) {
+    const int t = (int)threadIdx.x - t0;
+    if (t < 0) return;
     if (t < NV) {
         double s = 0.0;
         for (int w = 0; w < nwarps; ++w) s += (double)red[w * 12 + 2 * t] + (double)red[w * 12 + 2 * t + 1];
@@ -785,7 +787,11 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> 
             for (int r = tid; r < PD * PD; r += NT_F32) gather_row<3, ROWI>(sm, args, tab[0], r % PD, r / PD);
 
         for (;;) {
-            __syncthreads();
+            // an xyz item after an xyz item needs no barrier here: the last
+            // one closed the previous item's store, and each thread's sweep 1
+            // reads only its own row (the previous item's diagnostics are
+            // combined meanwhile by threads without a row)
+            if (ORDER == 1 || first) __syncthreads();
             const int next = s_item[1];
             const bool has_next = next < args.total;
             const ItemTab& cur = tab[slot];
@@ -827,7 +833,7 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> 
             }
             __syncthreads();
             if (tid == 0) s_cnt[0] = s_cnt[1] = 0;
-            if (diag) finish_diag(args.diag, cur_item, s_red, 8);
+            if (diag) finish_diag(args.diag, cur_item, s_red, 8, NT_F32 - 6);
             if (!has_next) break;
             slot ^= 1;
             if (ORDER == 1) {
@@ -987,7 +993,7 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_pair(const SweepArgs<float>
                 s_cnt[0] = s_cnt[1] = 0;
                 if (ord == 0) s_aux[0] = cur_g;       // published in the next phase 2, or below
             }
-            if (ord == 1 && diag) finish_diag(args.diag, cur_g, s_red, 8);
+            if (ord == 1 && diag) finish_diag(args.diag, cur_g, s_red, 8, NT_F32 - 6);
             if (!has_next) break;
             slot ^= 1;
             if (s_cnt[3] != 0) {
