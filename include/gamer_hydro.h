@@ -61,8 +61,10 @@ typedef struct gamer_hydro_s *gamer_hydro_t;
 
 /* One refinement level.  face_flux is optional: [n_groups][3][3][5][16][16]
  * of the element type (net interface fluxes on the interior-relative planes
- * 0, 8, 16 of each axis, for the 16x16 interior rows); when NULL and the
- * hierarchy has more than one level the handle allocates its own. */
+ * 0, 8, 16 of each axis, for the 16x16 interior rows), every plane written
+ * by each step; when NULL and the hierarchy has more than one level the
+ * handle allocates its own, into which FP32 steps may write only what the
+ * coarse-fine fix-ups read. */
 typedef struct {
     int32_t n_groups;
     int32_t reserved;

@@ -20,6 +20,13 @@ constexpr int PD = 22;     // padded size
 constexpr int MAXLEV = 16; // levels per launch
 constexpr int CELLS_PG = GS * GS * GS;          // 4096
 constexpr int FLUX_PG = 3 * 3 * NV * GS * GS;   // face-flux values per group
+// Coarse-fine ghost slot of one FP32 group: per variable and padded x-row
+// (zp, yp) 24 floats -- the 16 centre cells at 0..15, the -x edge (x = -3..-1)
+// at 16..18, the +x edge (x = 16..18) at 20..22 -- so every piece starts on
+// a 16-byte boundary.
+constexpr int GROW = 24;
+constexpr int GVS = PD * PD * GROW;             // floats per variable of a slot
+constexpr size_t GHOST_PG = (size_t)NV * GVS;   // floats per slot
 
 // One level as a kernel sees it.  All pointers are device memory.
 template <typename T>
@@ -32,13 +39,19 @@ struct LevelArgs {
     const T* uc;        // level-1 pre-step state (coarse ghosts)
     const T* ucn;       // level-1 state after its sweep set (individual time steps), or nullptr
     const int* nbrc;    // level-1 map
+    T* ghost;           // FP32: the coarse-fine ghost cells of this launch, formed by a pass before the
+                        // sweeps ([slot][5][22][22][24]), or nullptr (level 0, FP64)
+    const int* gslot;   // [n] slot of a group in ghost, -1 for a group with no coarse region
+    const int* slot_g;  // [n_slots] group of each slot
     int n_groups;
     int n_groups_c;
     int item0;          // first work item of this level in a multi-level launch
-    int pad_;
+    int n_slots;
     double dh;          // cell width; lambda = dt * dts / dh is formed on the device in FP64
     double dts;         // this level's share of the device dt: 1, or 2^-l with individual time steps
     double cw;          // time weight of ucn in the coarse ghosts (0 or 1/2)
+    const unsigned* fneed;  // FP32, handle-owned fluxes: [n] bit 4 ax + q set where the fix-ups read a
+                            // flux of the axis-ax sweep columns in transverse quarter q; nullptr: all
 };
 
 // Per-group diagnostic sinks (exact max of the signal speed, leaf sums of

@@ -37,6 +37,11 @@ struct LevelCache {
     int* d_fix_list = nullptr;
     void* own_flux = nullptr;     // handle-owned face fluxes when the caller gives none
     void* own_flux2 = nullptr;    // fluxes of a level's second step (individual time steps)
+    void* ghost = nullptr;        // FP32 coarse-fine ghost slots (levels above 0)
+    int* d_gslot = nullptr;       // [n_groups] slot of a group, -1 without a coarse region
+    int* d_slot_g = nullptr;      // [n_slots] group of each slot
+    int n_slots = 0;
+    unsigned* d_fneed = nullptr;  // [n_groups] face-flux columns the fix-ups read (FP32, own fluxes)
 };
 
 }  // namespace
@@ -150,13 +155,24 @@ void fill_level(LevelArgs<T>& a, const gamer_level_t* L, int l, const gamer_hydr
     a.nbr = c.nbr;
     a.flux = static_cast<T*>(c.face_flux ? c.face_flux : h->lv[l].own_flux);
     if (h->n_levels == 1) a.flux = nullptr;
+    // a caller's flux buffer gets every plane; the handle's own only what the fix-ups read
+    a.fneed = (c.face_flux == nullptr && h->precision == GAMER_FP32) ? h->lv[l].d_fneed : nullptr;
     a.parent = l > 0 ? c.parent : nullptr;
     a.uc = l > 0 ? static_cast<const T*>(L[l - 1].u) : nullptr;
     a.nbrc = l > 0 ? L[l - 1].nbr : nullptr;
+    a.ghost = nullptr;
+    a.gslot = nullptr;
+    a.slot_g = nullptr;
+    a.n_slots = 0;
+    if (l > 0 && h->precision == GAMER_FP32) {
+        a.ghost = static_cast<T*>(h->lv[l].ghost);
+        a.gslot = h->lv[l].d_gslot;
+        a.slot_g = h->lv[l].d_slot_g;
+        a.n_slots = h->lv[l].n_slots;
+    }
     a.n_groups = c.n_groups;
     a.n_groups_c = l > 0 ? L[l - 1].n_groups : 0;
     a.item0 = 0;
-    a.pad_ = 0;
     a.dh = c.dh;
     a.ucn = nullptr;
     a.dts = 1.0;
@@ -194,10 +210,28 @@ void drop_hierarchy(gamer_hydro_t h) {
         cudaFree(c.d_fix_list);
         cudaFree(c.own_flux);
         cudaFree(c.own_flux2);
+        cudaFree(c.ghost);
+        cudaFree(c.d_gslot);
+        cudaFree(c.d_slot_g);
+        cudaFree(c.d_fneed);
     }
     h->lv.clear();
     h->have_version = false;
     drop_graphs(h);
+}
+
+// Source of ghost region r = (oz+1)*9 + (oy+1)*3 + (ox+1) of group g: the
+// same-level group after the outflow clamp (axes whose face neighbour is -2
+// fold into the group), -1 for a region on the coarser level, -2 outside.
+int region_source(const std::vector<int>& nbr, int g, int r) {
+    int o[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
+    for (int a = 0; a < 3; ++a) {
+        if (o[a] == 0) continue;
+        int e[3] = {0, 0, 0};
+        e[a] = o[a];
+        if (nbr[(size_t)g * 26 + dir_index(e[0], e[1], e[2])] == -2) o[a] = 0;
+    }
+    return (o[0] | o[1] | o[2]) ? nbr[(size_t)g * 26 + dir_index(o[0], o[1], o[2])] : g;
 }
 
 // Validate a hierarchy snapshot (once per version) and build the fix-up
@@ -250,14 +284,7 @@ int prepare(gamer_hydro_t h, const gamer_hierarchy_t* H) {
         for (int g = 0; g < ng; ++g)
             for (int r = 0; r < 27; ++r) {
                 if (r == 13) continue;
-                int o[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
-                for (int a = 0; a < 3; ++a) {
-                    if (o[a] == 0) continue;
-                    int e[3] = {0, 0, 0};
-                    e[a] = o[a];
-                    if (nbr[l][(size_t)g * 26 + dir_index(e[0], e[1], e[2])] == -2) o[a] = 0;
-                }
-                const int src = (o[0] | o[1] | o[2]) ? nbr[l][(size_t)g * 26 + dir_index(o[0], o[1], o[2])] : g;
+                const int src = region_source(nbr[l], g, r);
                 if (src >= 0 || (src == -1 && l > 0)) continue;
                 return fail(h, GAMER_ERR_MAP, "ghost region of group " + std::to_string(g) + " on level " +
                                                   std::to_string(l) + " does not resolve");
@@ -297,6 +324,24 @@ int prepare(gamer_hydro_t h, const gamer_hierarchy_t* H) {
             CK(h, cudaMalloc(&c.own_flux, (size_t)c.n_groups * FLUX_PG * elem_size(h)));
         if (n > 1 && h->individual && c.n_groups > 0)
             CK(h, cudaMalloc(&c.own_flux2, (size_t)c.n_groups * FLUX_PG * elem_size(h)));
+        if (l > 0 && h->precision == GAMER_FP32 && c.n_groups > 0) {
+            // a slot for every group with a ghost region on the coarser level
+            std::vector<int> slot(c.n_groups, -1), slot_g;
+            for (int g = 0; g < c.n_groups; ++g)
+                for (int r = 0; r < 27 && slot[g] < 0; ++r)
+                    if (r != 13 && region_source(nbr[l], g, r) == -1) {
+                        slot[g] = (int)slot_g.size();
+                        slot_g.push_back(g);
+                    }
+            c.n_slots = (int)slot_g.size();
+            CK(h, cudaMalloc(&c.d_gslot, sizeof(int) * c.n_groups));
+            CK(h, cudaMemcpy(c.d_gslot, slot.data(), sizeof(int) * c.n_groups, cudaMemcpyHostToDevice));
+            if (c.n_slots > 0) {
+                CK(h, cudaMalloc(&c.ghost, (size_t)c.n_slots * GHOST_PG * sizeof(float)));
+                CK(h, cudaMalloc(&c.d_slot_g, sizeof(int) * c.n_slots));
+                CK(h, cudaMemcpy(c.d_slot_g, slot_g.data(), sizeof(int) * c.n_slots, cudaMemcpyHostToDevice));
+            }
+        }
         if (l + 1 < n) {
             for (int P = 0; P < 8 * c.n_groups; ++P) {
                 bool take = child[l][P] >= 0;
@@ -323,6 +368,40 @@ int prepare(gamer_hydro_t h, const gamer_hierarchy_t* H) {
                 CK(h, cudaMemcpy(c.d_fix_list, c.fix_list.data(), sizeof(int) * c.fix_list.size(),
                                  cudaMemcpyHostToDevice));
             }
+        }
+    }
+    // Face fluxes the fix-ups read (k_fixup), per group as bit 4 ax + q for
+    // the sweep columns along axis ax in transverse quarter q (q = 2 p_t2 +
+    // p_t1 over the patch positions along the transverse axes t1 < t2): a
+    // leaf patch's face towards a refined same-level patch (coarse side),
+    // and the whole face of the refined patch's child group towards it
+    // (fine side).
+    if (n > 1 && h->precision == GAMER_FP32) {
+        std::vector<std::vector<unsigned>> need(n);
+        for (int l = 0; l < n; ++l) need[l].assign(H->levels[l].n_groups, 0u);
+        for (int l = 0; l + 1 < n; ++l)
+            for (int P = 0; P < 8 * H->levels[l].n_groups; ++P) {
+                if (child[l][P] >= 0) continue;
+                const int g = P >> 3, lp = P & 7;
+                const int pc[3] = {lp & 1, (lp >> 1) & 1, (lp >> 2) & 1};
+                for (int ax = 0; ax < 3; ++ax)
+                    for (int s = -1; s <= 1; s += 2) {
+                        int q[3] = {pc[0], pc[1], pc[2]};
+                        q[ax] += s;
+                        const int gq = resolve_patch(nbr[l], g, q);
+                        if (gq < 0) continue;
+                        const int fq = child[l][8 * gq + (q[2] * 2 + q[1]) * 2 + q[0]];
+                        if (fq < 0) continue;
+                        const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
+                        need[l][g] |= 1u << (4 * ax + 2 * pc[t2] + pc[t1]);
+                        need[l + 1][fq] |= 0xFu << (4 * ax);
+                    }
+            }
+        for (int l = 0; l < n; ++l) {
+            LevelCache& c = h->lv[l];
+            if (c.n_groups == 0) continue;
+            CK(h, cudaMalloc(&c.d_fneed, sizeof(unsigned) * c.n_groups));
+            CK(h, cudaMemcpy(c.d_fneed, need[l].data(), sizeof(unsigned) * c.n_groups, cudaMemcpyHostToDevice));
         }
     }
     // A pair launch writes a group's zyx result over its input once the xyz

@@ -201,10 +201,24 @@ __device__ __forceinline__ const unsigned short* lane_map() {
     return S_IDX == 0 ? kLaneZyxS1 : S_IDX == 1 ? kLaneZyxS2 : kLaneZyxS3;
 }
 
+// Face-flux slot of the column at transverse position (i1, i2) of a sweep
+// along AX, or nullptr where the group has no flux buffer, the column is
+// not an interior one, or (MASK) no fix-up reads its fluxes (fm: bit 4 AX +
+// q for the transverse quarter q = 2 [(i2 - 3) >= 8] + [(i1 - 3) >= 8]).
+template <int AX, bool MASK>
+__device__ __forceinline__ float* flux_slot(float* flux_g, unsigned fm, int i1, int i2) {
+    float* fl = nullptr;
+    if (flux_g != nullptr && i1 >= NG && i1 < NG + GS && i2 >= NG && i2 < NG + GS &&
+        (!MASK || ((fm >> (4 * AX + 2 * ((i2 - NG) >> 3) + ((i1 - NG) >> 3))) & 1u)))
+        fl = flux_g + AX * (3 * NV * 256) + (i2 - NG) * GS + (i1 - NG);
+    return fl;
+}
+
 // Sweep s (0,1,2) of order ORDER over the shared block; columns whose
 // transverse axes were swept earlier in this set only cover [3,19).
-template <int ORDER, int S_IDX, int LIM>
-__device__ __forceinline__ void sweep(float* sm, float lam, float g, float gm1, float* flux_g, int nact) {
+template <int ORDER, int S_IDX, int LIM, bool MASK = false>
+__device__ __forceinline__ void sweep(float* sm, float lam, float g, float gm1, float* flux_g, int nact,
+                                      unsigned fm = 0xFFFu) {
     constexpr int AX = ORDER == 0 ? S_IDX : 2 - S_IDX;
     constexpr int T1 = AX == 0 ? 1 : 0;
     constexpr int T2 = AX == 2 ? 1 : 2;
@@ -229,10 +243,7 @@ __device__ __forceinline__ void sweep(float* sm, float lam, float g, float gm1, 
             i2 = LO2 + c / N1;
         }
         float* p = sm + i1 * ST[T1] + i2 * ST[T2];
-        float* fl = nullptr;
-        if (flux_g != nullptr && i1 >= NG && i1 < NG + GS && i2 >= NG && i2 < NG + GS)
-            fl = flux_g + AX * (3 * NV * 256) + (i2 - NG) * GS + (i1 - NG);
-        column<AX, S, LIM>(p, lam4, lam2, g, gm1, fl);
+        column<AX, S, LIM>(p, lam4, lam2, g, gm1, flux_slot<AX, MASK>(flux_g, fm, i1, i2));
     }
 }
 
@@ -250,7 +261,7 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
 // parent's coarse group, level, group index and parent patch.
 struct ItemTab {
     int src[27], mask[27], csrc[27], cmask[27];
-    int item, level, g, par;
+    int item, level, g, par, gslot;
     float lam;          // dt / dh, formed in FP64 from the device time step
 };
 
@@ -275,6 +286,7 @@ __device__ __forceinline__ void build_tab(ItemTab& t, const SweepArgs<float>& a,
         t.level = l;
         t.g = g;
         t.par = L.parent != nullptr ? L.parent[g] : -1;
+        t.gslot = L.gslot != nullptr ? L.gslot[g] : -1;
         t.lam = (float)((*a.dt * L.dts) / L.dh);
     }
 }
@@ -302,101 +314,14 @@ __device__ __noinline__ void prolong_cell(const LevelArgs<float>& L, const ItemT
                    (lp >> 2) & 1, x, y, z, val);
 }
 
-// Coarse-fine ghost cells x in [xa, xb) of the fine row (y, z) (group-local
-// fine coordinates, xb - xa <= 8: one half of the row's centre or one
-// edge) by Min-Mod interpolation, the same arithmetic as prolong_cell:
-// the row's coarse cells (x >> 1) are read once -- the coarse row with its
-// x-neighbours and the four side rows, every load of a variable issued
-// before the first is used -- and each coarse cell's limited slopes serve
-// both of its fine children.  dst: the shared-memory cell of x = xa,
-// variable 0.  Out of line like prolong_cell.
-__device__ __noinline__ void prolong_row(const LevelArgs<float>& L, const ItemTab& t, int y, int z, int xa, int xb,
-                                         float* dst) {
-    constexpr int MC = 4;                                  // coarse cells per call, at most
-    const int lp = t.par & 7;
-    const int px = lp & 1, py = (lp >> 1) & 1, pz = (lp >> 2) & 1;
-    const int cy = PS * py + (y >> 1), cz = PS * pz + (z >> 1);
-    const int ca = PS * px + (xa >> 1);
-    const int nc = PS * px + ((xb - 1) >> 1) - ca + 1;
-    const float sy = (y & 1) ? 1.0f : -1.0f, sz = (z & 1) ? 1.0f : -1.0f;
-    auto at = [&](int a, int b, int c) -> int {
-        const int s = resolve(t.csrc, t.cmask, a, b, c);
-        return (int)cell_offset(s < 0 ? 0 : s, a, b, c);   // s < 0 cannot pass host validation
-    };
-    // coarse row ca-1 .. ca+nc, side rows y-1, y+1, z-1, z+1 at ca .. ca+nc-1
-    int oc[MC + 2], oym[MC], oyp[MC], ozm[MC], ozp[MC];
-#pragma unroll
-    for (int i = 0; i < MC + 2; ++i)
-        if (i < nc + 2) oc[i] = at(ca - 1 + i, cy, cz);
-#pragma unroll
-    for (int i = 0; i < MC; ++i) {
-        if (i >= nc) continue;
-        oym[i] = at(ca + i, cy - 1, cz);
-        oyp[i] = at(ca + i, cy + 1, cz);
-        ozm[i] = at(ca + i, cy, cz - 1);
-        ozp[i] = at(ca + i, cy, cz + 1);
-    }
-    const size_t vs = (size_t)L.n_groups_c * 8 * 512;
-    const float w = (float)L.cw;
-#pragma unroll 1
-    for (int v = 0; v < NV; ++v) {
-        const float* p = L.uc + v * vs;
-        const float* pn = L.ucn != nullptr ? L.ucn + v * vs : nullptr;
-        float c[MC + 2], ym[MC], yp[MC], zm[MC], zp[MC];
-#pragma unroll
-        for (int i = 0; i < MC + 2; ++i)
-            if (i < nc + 2) c[i] = p[oc[i]];
-#pragma unroll
-        for (int i = 0; i < MC; ++i) {
-            if (i >= nc) continue;
-            ym[i] = p[oym[i]];
-            yp[i] = p[oyp[i]];
-            zm[i] = p[ozm[i]];
-            zp[i] = p[ozp[i]];
-        }
-        if (pn != nullptr) {
-            // individual time steps: the coarse state at the start of this
-            // level's step, linear in time between before and after the
-            // coarse sweep set
-#pragma unroll
-            for (int i = 0; i < MC + 2; ++i)
-                if (i < nc + 2) c[i] = c[i] + w * (pn[oc[i]] - c[i]);
-#pragma unroll
-            for (int i = 0; i < MC; ++i) {
-                if (i >= nc) continue;
-                ym[i] = ym[i] + w * (pn[oym[i]] - ym[i]);
-                yp[i] = yp[i] + w * (pn[oyp[i]] - yp[i]);
-                zm[i] = zm[i] + w * (pn[ozm[i]] - zm[i]);
-                zp[i] = zp[i] + w * (pn[ozp[i]] - zp[i]);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < MC; ++i) {
-            if (i >= nc) continue;
-            const float U = c[i + 1];
-            const float Sx = minmod_slope(c[i], U, c[i + 2]);
-            const float Sy = minmod_slope(ym[i], U, yp[i]);
-            const float Sz = minmod_slope(zm[i], U, zp[i]);
-            const int x0 = 2 * (ca + i - PS * px);               // fine x of the child with sx = -1
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) {
-                const int x = x0 + dx;
-                if (x < xa || x >= xb) continue;
-                const float sx = dx ? 1.0f : -1.0f;
-                const float tt = (sx * Sx + sy * Sy) + sz * Sz;
-                dst[v * VS + (x - xa)] = U + 0.25f * tt;
-            }
-        }
-    }
-}
-
 // One padded x-row (yp, zp) of the block of item t.  SEG bit 0: the 16
 // centre cells (x in [0,16)); bit 1: the 3 + 3 edge cells; bit 2 / bit 3:
 // only the first / second half of the centre (one patch row each).  Every cell lies
 // in an aligned quad of a patch row of its source group, so the centre is
 // four 16-byte loads per variable and each edge one.  Outflow edges repeat
-// the centre's edge cell (zero gradient); cells of coarse regions are
-// interpolated one by one.
+// the centre's edge cell (zero gradient).  Cells of coarse regions are read
+// from the group's ghost slot in ROWI launches (one 16-byte load per
+// piece, like a same-level row) and interpolated one by one otherwise.
 template <int SEG, bool ROWI = false>
 __device__ __forceinline__ void gather_row(float* sm, const SweepArgs<float>& a, const ItemTab& t,
                                            int yp, int zp) {
@@ -408,19 +333,27 @@ __device__ __forceinline__ void gather_row(float* sm, const SweepArgs<float>& a,
     const int sc = resolve(t.src, t.mask, xc, yc, zc);
     const size_t offc = sc >= 0 ? cell_offset(sc, 0, yc, zc) : 0;
     constexpr bool H0 = (SEG & 1) || (SEG & 4), H1 = (SEG & 1) || (SEG & 8);
+    // ROWI: the launch's coarse-fine ghost cells were formed before it, in
+    // the group's ghost slot (k_ghost_f32)
+    const float* gp = ROWI && t.gslot >= 0 ? L.ghost + (size_t)t.gslot * GHOST_PG + (zp * PD + yp) * GROW : nullptr;
     if (H0 || H1) {
-        if (sc >= 0) {
+        if (sc >= 0 || ROWI) {
+            // the row's centre from its group (patch px = 1 at +512) or from
+            // the ghost slot (x = 8 at +8)
+            const float* p0 = sc >= 0 ? L.u + offc : gp;
+            const size_t vst = sc >= 0 ? vstride : (size_t)GVS;
+            const int o1 = sc >= 0 ? 512 : PS;
             float4 c[NV][4];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                const float* p = L.u + v * vstride + offc;
+                const float* p = p0 + v * vst;
                 if (H0) {
                     c[v][0] = ldg4(p);
                     c[v][1] = ldg4(p + 4);
                 }
                 if (H1) {
-                    c[v][2] = ldg4(p + 512);   // patch px = 1
-                    c[v][3] = ldg4(p + 516);
+                    c[v][2] = ldg4(p + o1);
+                    c[v][3] = ldg4(p + o1 + 4);
                 }
             }
 #pragma unroll
@@ -435,9 +368,6 @@ __device__ __forceinline__ void gather_row(float* sm, const SweepArgs<float>& a,
                     q[4 * j + 3] = c[v][j].w;
                 }
             }
-        } else if (ROWI) {
-            if (H0) prolong_row(L, t, y, z, 0, PS, d + NG);
-            if (H1) prolong_row(L, t, y, z, PS, GS, d + NG + PS);
         } else {
             for (int x = H0 ? 0 : PS; x < (H1 ? GS : PS); ++x) {
                 float val[NV];
@@ -458,6 +388,9 @@ __device__ __forceinline__ void gather_row(float* sm, const SweepArgs<float>& a,
                 if (sc >= 0) {
 #pragma unroll
                     for (int v = 0; v < NV; ++v) val[v] = L.u[v * vstride + offc + (side ? 512 + 7 : 0)];
+                } else if (ROWI) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) val[v] = gp[v * GVS + (side ? GS - 1 : 0)];
                 } else {
                     prolong_cell(L, t, side ? GS - 1 : 0, y, z, val);
                 }
@@ -484,7 +417,14 @@ __device__ __forceinline__ void gather_row(float* sm, const SweepArgs<float>& a,
                     }
                 }
             } else if (ROWI) {
-                prolong_row(L, t, y, z, side ? GS : -NG, side ? GS + NG : 0, d + o);
+                // x = -3..-1 at 16, x = 16..18 at 20
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const float4 q = ldg4(gp + v * GVS + (side ? 20 : 16));
+                    d[v * VS + o] = q.x;
+                    d[v * VS + o + 1] = q.y;
+                    d[v * VS + o + 2] = q.z;
+                }
             } else {
                 for (int k = 0; k < NG; ++k) {
                     float val[NV];
@@ -551,6 +491,108 @@ __device__ __forceinline__ void gather_pool(float* sm, const SweepArgs<float>& a
     }
 }
 
+// Coarse-fine ghost cells of a launch (Sec. 2.2: Min-Mod interpolation from
+// the coarser level), formed before its sweeps: one block per ghost slot of
+// the levels from lc on, i.e. per group with a region on the coarser
+// level, which fills those regions' cells in its slot, a thread per coarse cell
+// under them (the padded block spans coarse cells -2..9 per axis: 2, 8, 2
+// per region along each axis): the cell, its six neighbours and its three
+// limited slopes are read and formed once and give all of its children
+// inside the block -- the arithmetic of prolong_cell, child by child.  The
+// children of one coarse cell lie in one region (region edges are even in
+// fine cells), which decides: a region is filled where its source is the
+// coarser level, except x-edges clamped at an outflow face (those repeat
+// the centre's edge cell, read from the slot).  The sweep launch that
+// follows on the stream copies the slot like same-level ghosts, so no phase
+// of a sweep block waits on an interpolation.
+constexpr int NT_GHOST = 256;
+
+__global__ void __launch_bounds__(NT_GHOST) k_ghost_f32(const SweepArgs<float> a, int lc) {
+    __shared__ ItemTab t;
+    __shared__ int s_off[28];          // first task of each region (prefix sums of their coarse cells)
+    int l = lc, b = (int)blockIdx.x;
+    while (b >= a.lv[l].n_slots) b -= a.lv[l].n_slots, ++l;
+    const LevelArgs<float>& L = a.lv[l];
+    build_tab(t, a, L.item0 + L.slot_g[b], 0);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int r = threadIdx.x;
+        const int rx = r % 3 - 1;
+        int n = 0;
+        if (r < 27 && r != 13 && t.src[r] < 0 && !(rx != 0 && (t.mask[r] & 1)))
+            n = (rx ? 2 : PS) * ((r / 3) % 3 == 1 ? PS : 2) * (r / 9 == 1 ? PS : 2);
+        // inclusive warp scan
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int m = __shfl_up_sync(0xffffffffu, n, d);
+            if (r >= d) n += m;
+        }
+        if (r < 27) s_off[r + 1] = n;
+        if (r == 0) s_off[0] = 0;
+    }
+    __syncthreads();
+    float* G = L.ghost + (size_t)t.gslot * GHOST_PG;
+    const int lp = t.par & 7;
+    const int px = PS * (lp & 1), py = PS * ((lp >> 1) & 1), pz = PS * ((lp >> 2) & 1);
+    const size_t vs = (size_t)L.n_groups_c * 8 * 512;
+    const float w = (float)L.cw;
+    for (int i = threadIdx.x; i < s_off[27]; i += NT_GHOST) {
+        int r = 0;
+        while (s_off[r + 1] <= i) ++r;
+        const int rx = r % 3 - 1, ry = (r / 3) % 3 - 1, rz = r / 9 - 1;
+        const int nx = rx ? 2 : PS, ny = ry ? 2 : PS;
+        const int j = i - s_off[r];
+        // region -1: coarse -2, -1; region 0: 0..7; region +1: 8, 9
+        const int cx = (rx < 0 ? -2 : (rx > 0 ? PS : 0)) + j % nx;
+        const int cy = (ry < 0 ? -2 : (ry > 0 ? PS : 0)) + (j / nx) % ny;
+        const int cz = (rz < 0 ? -2 : (rz > 0 ? PS : 0)) + j / (nx * ny);
+        // the coarse cell and its six neighbours in the parent's coarse group
+        const int X = px + cx, Y = py + cy, Z = pz + cz;
+        auto at = [&](int u, int v, int q) -> size_t {
+            const int s = resolve(t.csrc, t.cmask, u, v, q);
+            return cell_offset(s < 0 ? 0 : s, u, v, q);     // s < 0 cannot pass host validation
+        };
+        const size_t o[7] = {at(X, Y, Z),     at(X - 1, Y, Z), at(X + 1, Y, Z), at(X, Y - 1, Z),
+                             at(X, Y + 1, Z), at(X, Y, Z - 1), at(X, Y, Z + 1)};
+        // children inside the padded block: fine 2c + d in [-3, 19)
+        const int d0x = cx == -2 ? 1 : 0, d1x = cx == 9 ? 0 : 1;
+        const int d0y = cy == -2 ? 1 : 0, d1y = cy == 9 ? 0 : 1;
+        const int d0z = cz == -2 ? 1 : 0, d1z = cz == 9 ? 0 : 1;
+#pragma unroll 1
+        for (int v = 0; v < NV; ++v) {
+            const float* p = L.uc + v * vs;
+            float c[7];
+#pragma unroll
+            for (int q = 0; q < 7; ++q) c[q] = p[o[q]];
+            if (L.ucn != nullptr) {
+                // individual time steps: the coarse state at the start of
+                // this level's step, linear in time between before and after
+                // the coarse sweep set
+                const float* pn = L.ucn + v * vs;
+#pragma unroll
+                for (int q = 0; q < 7; ++q) c[q] = c[q] + w * (pn[o[q]] - c[q]);
+            }
+            const float U = c[0];
+            const float Sx = minmod_slope(c[1], U, c[2]);
+            const float Sy = minmod_slope(c[3], U, c[4]);
+            const float Sz = minmod_slope(c[5], U, c[6]);
+            float* gv = G + v * GVS;
+            for (int dz = d0z; dz <= d1z; ++dz)
+                for (int dy = d0y; dy <= d1y; ++dy) {
+                    const int fy = 2 * cy + dy, fz = 2 * cz + dz;
+                    float* row = gv + ((fz + NG) * PD + (fy + NG)) * GROW;
+                    const float sy = dy ? 1.0f : -1.0f, sz = dz ? 1.0f : -1.0f;
+                    for (int dx = d0x; dx <= d1x; ++dx) {
+                        const int fx = 2 * cx + dx;
+                        const float sx = dx ? 1.0f : -1.0f;
+                        const float tt = (sx * Sx + sy * Sy) + sz * Sz;
+                        row[fx < 0 ? GS + NG + fx : (fx >= GS ? fx + 4 : fx)] = U + 0.25f * tt;
+                    }
+                }
+        }
+    }
+}
+
 // Double-float (hi, lo) accumulation, error-free in each step (two-sum).
 __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
     const float s = hi + x;
@@ -612,9 +654,10 @@ struct DiagAcc {
 // per patch row and variable; z-columns: one store per cell and variable,
 // coalesced across the warp's consecutive x) and, with diagnostics on,
 // accumulates them and parks the warp's result in red.
-template <int ORDER, int LIM>
+template <int ORDER, int LIM, bool MASK = false>
 __device__ __forceinline__ void sweep_last_store(float* sm, float lam, float g, float gm1, float* flux_g,
-                                                 const LevelArgs<float>& L, int grp, bool diag, float* red) {
+                                                 const LevelArgs<float>& L, int grp, bool diag, float* red,
+                                                 unsigned fm = 0xFFFu) {
     constexpr int AX = ORDER == 0 ? 2 : 0;
     constexpr int T1 = AX == 0 ? 1 : 0;
     constexpr int T2 = AX == 2 ? 1 : 2;
@@ -629,6 +672,7 @@ __device__ __forceinline__ void sweep_last_store(float* sm, float lam, float g, 
     }
     float* p = sm + i1 * ST[T1] + i2 * ST[T2];
     float* fl = flux_g ? flux_g + AX * (3 * NV * 256) + (i2 - NG) * GS + (i1 - NG) : nullptr;
+    if (MASK && !((fm >> (4 * AX + 2 * ((i2 - NG) >> 3) + ((i1 - NG) >> 3))) & 1u)) fl = nullptr;
     column<AX, S, LIM>(p, 0.25f * lam, 0.5f * lam, g, gm1, fl);
     const size_t vstride = (size_t)L.n_groups * 8 * 512;
     DiagAcc acc;
@@ -735,7 +779,7 @@ constexpr int NT_F32 = 512;
 
 template <int ORDER, int LIM, bool ROWI = false>
 __device__ __forceinline__ void sweep_first(float* sm, const SweepArgs<float>& a, const ItemTab& t,
-                                            float lam, float* flux_g, bool whole = false) {
+                                            float lam, float* flux_g, bool whole = false, unsigned fm = 0xFFFu) {
     if (ORDER == 0) {
         // x-rows (yp, zp); rows with yp in [3,19) get their centre first --
         // with `whole` (the first item of a CTA, nothing gathered before)
@@ -747,19 +791,16 @@ __device__ __forceinline__ void sweep_first(float* sm, const SweepArgs<float>& a
         if (whole) gather_row<3, ROWI>(sm, a, t, yp, zp);
         else if (yp >= NG && yp < NG + GS) gather_row<1, ROWI>(sm, a, t, yp, zp);
         float* p = sm + yp * XP + zp * (PD * XP);
-        float* fl = nullptr;
-        if (flux_g != nullptr && yp >= NG && yp < NG + GS && zp >= NG && zp < NG + GS)
-            fl = flux_g + (zp - NG) * GS + (yp - NG);
-        column<0, 1, LIM>(p, 0.25f * lam, 0.5f * lam, a.gamma, a.gm1, fl);
+        column<0, 1, LIM>(p, 0.25f * lam, 0.5f * lam, a.gamma, a.gm1, flux_slot<0, ROWI>(flux_g, fm, yp, zp));
     } else {
-        sweep<ORDER, 0, LIM>(sm, lam, a.gamma, a.gm1, flux_g, NT_F32);
+        sweep<ORDER, 0, LIM, ROWI>(sm, lam, a.gamma, a.gm1, flux_g, NT_F32, fm);
     }
 }
 
-// ROWI: coarse-fine ghost rows interpolated a row segment per call
-// (prolong_row), for launches that include a level with a coarser level;
-// launches over level 0 alone have no coarse regions and keep the per-cell
-// fallback, whose code is smaller.
+// ROWI: launches that include a level with a coarser level, whose
+// coarse-fine ghost cells k_ghost_f32 formed before the launch; launches
+// over level 0 alone have no coarse regions and keep the per-cell fallback,
+// whose code is smaller.
 template <int ORDER, int LIM, bool ROWI>
 __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> args) {
     extern __shared__ float sm[];
@@ -801,12 +842,15 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> 
             const float lam = cur.lam;
             const int cur_item = cur.item;
             const int cur_g = cur.g;
+            // the face-flux columns the fix-ups read: every column in
+            // launches over level 0 alone (their kernels stay smaller)
+            const unsigned fm = ROWI && fg != nullptr && L.fneed != nullptr ? __ldg(L.fneed + cur_g) : 0xFFFu;
 
-            sweep_first<ORDER, LIM, ROWI>(sm, args, cur, lam, fg, first);
+            sweep_first<ORDER, LIM, ROWI>(sm, args, cur, lam, fg, first, fm);
             first = false;
             __syncthreads();
             if (tid < 11 * 32) {
-                sweep<ORDER, 1, LIM>(sm, lam, args.gamma, args.gm1, fg, 11 * 32);
+                sweep<ORDER, 1, LIM, ROWI>(sm, lam, args.gamma, args.gm1, fg, 11 * 32, fm);
                 if (ROWI && has_next) {
                     // coarse-fine rows make the gather pool long: the sweeping
                     // warps take what is left of it once the tables are built
@@ -822,7 +866,7 @@ __global__ void __launch_bounds__(NT_F32, 1) k_sweep_f32(const SweepArgs<float> 
             }
             __syncthreads();
             if (tid < 8 * 32) {
-                sweep_last_store<ORDER, LIM>(sm, lam, args.gamma, args.gm1, fg, L, cur_g, diag, s_red);
+                sweep_last_store<ORDER, LIM, ROWI>(sm, lam, args.gamma, args.gm1, fg, L, cur_g, diag, s_red, fm);
                 if (tid == 0) {
                     s_item[0] = next;
                     s_item[1] = has_next ? atomicAdd(args.queue, 1) : next;
@@ -1091,10 +1135,23 @@ cudaError_t sweep_f32_init() {
 
 template <int ORDER, int LIM>
 static cudaError_t launch_pipe(const SweepArgs<float>& a, int grid, cudaStream_t st) {
-    bool coarse = false;                 // some level of the launch has a coarser level
-    for (int l = 0; l < a.n_levels; ++l) coarse = coarse || a.lv[l].uc != nullptr;
-    if (coarse) k_sweep_f32<ORDER, LIM, true><<<grid, NT_F32, SMEM_F32, st>>>(a);
-    else k_sweep_f32<ORDER, LIM, false><<<grid, NT_F32, SMEM_F32, st>>>(a);
+    int lc = -1;                         // the first level of the launch with a coarser level
+    for (int l = a.n_levels - 1; l >= 0; --l)
+        if (a.lv[l].uc != nullptr) lc = l;
+    if (lc < 0) {
+        k_sweep_f32<ORDER, LIM, false><<<grid, NT_F32, SMEM_F32, st>>>(a);
+        return cudaGetLastError();
+    }
+    // every level from lc on has a coarser level and its ghost slot maps
+    int n = 0;
+    for (int l = lc; l < a.n_levels; ++l) {
+        const LevelArgs<float>& L = a.lv[l];
+        if (L.n_groups > 0 && (L.uc == nullptr || L.gslot == nullptr || (L.n_slots > 0 && L.slot_g == nullptr)))
+            return cudaErrorInvalidValue;
+        n += L.n_slots;
+    }
+    if (n > 0) k_ghost_f32<<<n, NT_GHOST, 0, st>>>(a, lc);
+    k_sweep_f32<ORDER, LIM, true><<<grid, NT_F32, SMEM_F32, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -449,6 +449,30 @@ def test_every_tuned_configuration_is_bit_identical(tmp_path, prec):
         S.close()
 
 
+def test_ghost_slots_equal_per_cell_interpolation_individual_steps(tmp_path):
+    """Individual time steps (coarse ghosts interpolated in time, then in
+    space): the pipelined FP32 sweep, whose coarse-fine ghost cells come
+    from the pass that fills each group's ghost slot before the launch,
+    against the non-pipelined variant, which interpolates every such cell
+    inside the sweep: bit-identical states on every level after two cycles."""
+    H, st = amr_case()
+    outs = []
+    for i, cfg in enumerate(["0,512,0,256", "1,512,0,256"]):
+        S = B.Solver(G, 0, B.GAMER_FP32)
+        D = B.DeviceHierarchy(H, st, torch.float32)
+        cache = tmp_path / f"tune{i}.txt"
+        _forced(cache, S, H, D, cfg)
+        B.gamer_hydro_tune(S.h, D, str(cache))
+        B.gamer_hydro_set_time_steps(S.h, B.GAMER_TIME_STEPS_INDIVIDUAL)
+        for _ in range(2):
+            B.gamer_hydro_step_pair(S.h, D, 0.5)
+        torch.cuda.synchronize()
+        outs.append(D.states())
+        S.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b, equal_nan=True)
+
+
 def test_fp64_groups_per_launch_do_not_change_results():
     """gamer_hydro_set_launch_groups: one patch group per launch (the plain
     layout), three per launch and the default batch give the same FP64
