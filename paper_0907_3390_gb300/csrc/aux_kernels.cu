@@ -18,6 +18,7 @@ namespace gh {
 // z-, z+.
 template <typename T>
 __global__ void __launch_bounds__(512) k_fixup(const FixArgs<T> a) {
+    using V2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
     __shared__ double s_lam;
     if (threadIdx.x == 0) s_lam = (*a.dt * a.dts) / a.dh;   // coarse lambda = dt / dh
     __syncthreads();
@@ -39,10 +40,13 @@ __global__ void __launch_bounds__(512) k_fixup(const FixArgs<T> a) {
 #pragma unroll
             for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
-                for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-                    for (int dx = 0; dx < 2; ++dx)
-                        s = s + f[cell_offset(gf, 2 * ci[0] + dx, 2 * ci[1] + dy, 2 * ci[2] + dz)];
+                for (int dy = 0; dy < 2; ++dy) {
+                    // the two x-children in one aligned load, added in order
+                    const V2 c = *reinterpret_cast<const V2*>(f + cell_offset(gf, 2 * ci[0], 2 * ci[1] + dy,
+                                                                               2 * ci[2] + dz));
+                    s = s + c.x;
+                    s = s + c.y;
+                }
             a.uc[v * vsc + co] = T(0.125) * s;
         }
         return;
@@ -170,17 +174,11 @@ __global__ void __launch_bounds__(NT_DIAG) k_diag(const DiagArgs<T> a) {
     Bits smax_t = 0;
     Acc acc[NV];
     int bad = 0;
-#pragma unroll 4
-    for (int i = threadIdx.x; i < CELLS_PG; i += NT_DIAG) {
-        const int patch = i >> 9;
-        const bool leaf = L.child == nullptr || L.child[8 * g + patch] < 0;
-        T u[NV];
+    // one cell of the group (fixed assignment of cells to threads)
+    auto cell = [&](const T u[NV], bool leaf) {
         bool finite = true;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            u[v] = base[v * vstride + i];
-            finite = finite && isfinite(u[v]);
-        }
+        for (int v = 0; v < NV; ++v) finite = finite && isfinite(u[v]);
         T s, P;
         speed_pressure(u, a.gamma, a.gm1, s, P);
         Bits sb;
@@ -190,6 +188,45 @@ __global__ void __launch_bounds__(NT_DIAG) k_diag(const DiagArgs<T> a) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) acc[v].add(u[v]);
             if (!finite || !(u[0] > T(0)) || !(P > T(0))) ++bad;
+        }
+    };
+    if constexpr (sizeof(T) == 4) {
+        // FP32: thread t takes the aligned quads t, t + 256, ... (all 20 of
+        // its 16-byte loads in flight before the first cell is formed)
+        constexpr int NQ = CELLS_PG / 4 / NT_DIAG;
+        float4 w[NQ][NV];
+#pragma unroll
+        for (int k = 0; k < NQ; ++k)
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+                w[k][v] = __ldg(reinterpret_cast<const float4*>(base + v * vstride) + threadIdx.x + k * NT_DIAG);
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+            const int patch = (threadIdx.x + k * NT_DIAG) >> 7;      // 128 quads per patch
+            const bool leaf = L.child == nullptr || L.child[8 * g + patch] < 0;
+            T u[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) u[v] = w[k][v].x;
+            cell(u, leaf);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) u[v] = w[k][v].y;
+            cell(u, leaf);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) u[v] = w[k][v].z;
+            cell(u, leaf);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) u[v] = w[k][v].w;
+            cell(u, leaf);
+        }
+    } else {
+#pragma unroll 4
+        for (int i = threadIdx.x; i < CELLS_PG; i += NT_DIAG) {
+            const int patch = i >> 9;
+            const bool leaf = L.child == nullptr || L.child[8 * g + patch] < 0;
+            T u[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) u[v] = base[v * vstride + i];
+            cell(u, leaf);
         }
     }
     T smax_v;
