@@ -287,6 +287,29 @@ def test_per_level_calls_equal_advance_all():
         S2.close()
 
 
+@pytest.mark.parametrize("individual", [False, True])
+def test_own_face_fluxes_equal_caller_fluxes(individual):
+    """FP32 steps into the handle's own face-flux buffers, which receive only
+    the columns the coarse-fine fix-ups read, against the same steps into
+    caller-given buffers, which receive every plane: bit-identical states
+    on every level (a column the fix-ups need but the mask left out would
+    be read from unwritten memory)."""
+    H, st = amr_case()
+    outs = []
+    for with_flux in (False, True):
+        S = B.Solver(G, 0, B.GAMER_FP32)
+        if individual:
+            B.gamer_hydro_set_time_steps(S.h, B.GAMER_TIME_STEPS_INDIVIDUAL)
+        D = B.DeviceHierarchy(H, st, torch.float32, with_flux=with_flux)
+        for _ in range(2):
+            B.gamer_hydro_step_pair(S.h, D, 0.5)
+        torch.cuda.synchronize()
+        outs.append(D.states())
+        S.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b, equal_nan=True)
+
+
 def test_amr_uniform_flow_bitwise():
     H, _ = amr_case()
     # dyadic values: the 8-child sums of the restriction are exact
