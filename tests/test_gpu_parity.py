@@ -264,6 +264,60 @@ def test_amr_fp32_and_composite_conservation():
     S.close()
 
 
+def outflow_corner_case():
+    """Three levels over a 32^3 base with outflow faces on every axis,
+    refined around one corner (64 / 56 / 56 patches): the fine groups touch
+    one, two or three outflow faces and have coarse regions inward, so
+    coarse-fine ghost regions are clamped at the faces (x-edges there
+    repeat the centre's edge cell)."""
+    def score(level, centres):
+        x, y, z = (centres[a][:, 0, 0, 0] for a in range(3))
+        return (0.45 if level == 0 else 0.2) - np.sqrt(x * x + y * y + z * z)
+    H = hm.build_hierarchy((2, 2, 2), score, 3, bc=("outflow",) * 3)
+
+    def prim(x, y, z, dh):
+        rho = 1.0 + 0.3 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y) + 0.2 * np.sin(2 * np.pi * z)
+        return (rho, 0.1 * np.cos(2 * np.pi * y), -0.05 * np.sin(2 * np.pi * z), 0.07 * np.cos(2 * np.pi * x),
+                1.0 + 0.1 * np.sin(2 * np.pi * (x + y)))
+    return H, wl.level_fields(H, prim)
+
+
+def test_outflow_corner_amr_matches_oracle():
+    H, st = outflow_corner_case()
+    assert H.patch_counts() == [64, 56, 56]
+    O, out = run_pair(H, st, F64, 4)
+    for l in range(3):
+        assert np.array_equal(out[l], O.u[l]), l
+    O, out = run_pair(H, st, F32, 4)
+    for l in range(3):
+        L1, mx = rel_err(out[l], O.u[l])
+        assert L1.max() <= 5e-6 and mx.max() <= 5e-4, (l, L1, mx)
+
+
+@pytest.mark.parametrize("individual", [False, True])
+def test_outflow_corner_ghost_slots_equal_per_cell_interpolation(tmp_path, individual):
+    """The ghost pass's clamped regions at outflow faces: the pipelined FP32
+    sweep (ghost slots) against the non-pipelined one (every coarse-fine
+    ghost cell interpolated inside the sweep), bit for bit."""
+    H, st = outflow_corner_case()
+    outs = []
+    for i, cfg in enumerate(["0,512,0,256", "1,512,0,256"]):
+        S = B.Solver(G, 0, B.GAMER_FP32)
+        D = B.DeviceHierarchy(H, st, torch.float32)
+        cache = tmp_path / f"tune{i}.txt"
+        _forced(cache, S, H, D, cfg)
+        B.gamer_hydro_tune(S.h, D, str(cache))
+        if individual:
+            B.gamer_hydro_set_time_steps(S.h, B.GAMER_TIME_STEPS_INDIVIDUAL)
+        for _ in range(2):
+            B.gamer_hydro_step_pair(S.h, D, 0.5)
+        torch.cuda.synchronize()
+        outs.append(D.states())
+        S.close()
+    for a, b in zip(*outs):
+        assert np.all(np.isfinite(a)) and np.array_equal(a, b)
+
+
 def test_per_level_calls_equal_advance_all():
     H, st = amr_case()
     for prec in (F64, F32):
