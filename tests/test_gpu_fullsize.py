@@ -11,7 +11,9 @@ plain FP64 path, then the fix-ups and the diagnostics).
   patches): two steps, every cell compared.
 * four-level stress hierarchies (32,768 patches): lognormal sigma 2.5 with
   Mach-20 flows, and a Sedov point blast: two steps, every cell compared,
-  composite conservation checked.
+  composite conservation checked; on the Sedov hierarchy the pipelined FP32
+  sweep (coarse-fine ghosts from the ghost pass) equals the non-pipelined
+  one (per-cell interpolation) bit for bit.
 
 Tolerances: FP64 bit-identical (and <= 1e-12 relative); FP32 per-field L1
 and max relative to the field's scale, two steps: L1 <= 1e-7 and max <=
@@ -147,6 +149,32 @@ def test_amr_three_levels_full():
     H, st = wl.amr_grf()
     assert H.patch_counts() == [4096, 9000, 21000]
     amr_compare(H, st, 2, (1e-7, 1e-5))
+
+
+def test_amr_four_level_ghost_slots_equal_per_cell_interpolation(tmp_path):
+    """The four-level Sedov hierarchy (ghost slots on three levels in one
+    launch): the pipelined FP32 sweep, whose coarse-fine ghost cells come
+    from the ghost pass, against the non-pipelined one, which interpolates
+    each of them inside its sweep, bit for bit after two pairs."""
+    H, st = wl.amr_stress("sedov")
+    outs = []
+    for i, cfg in enumerate(["0,512,0,256", "1,512,0,256"]):
+        S = B.Solver(G, B.GAMER_LIMITER_VANLEER, B.GAMER_FP32)
+        D = B.DeviceHierarchy(H, st, torch.float32)
+        # a tuning cache that names this configuration for this hierarchy
+        probe = tmp_path / f"probe{i}.txt"
+        B.gamer_hydro_tune(S.h, D, str(probe))
+        key = open(probe).read().strip().split("=")[0]
+        cache = tmp_path / f"tune{i}.txt"
+        cache.write_text(f"{key}={cfg}\n")
+        B.gamer_hydro_tune(S.h, D, str(cache))
+        for _ in range(2):
+            B.gamer_hydro_step_pair(S.h, D, CFL)
+        torch.cuda.synchronize()
+        outs.append(D.states())
+        S.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b, equal_nan=True)
 
 
 @pytest.mark.parametrize("kind", ["lognormal", "sedov"])
